@@ -1,0 +1,191 @@
+/*
+ * sw.h -- C ABI of the GB300 Swendsen-Wang sweep library (libsw_gb300.so).
+ *
+ * The library advances periodic L x L lattices of the q-state Potts model
+ * (Komura & Okabe, arXiv:1202.0635, Sec. 2, Eq. 1; Ising = Potts q = 2 in
+ * Ising units) and of the q-state clock model (Sec. 4, Eq. clock) by the
+ * Swendsen-Wang multi-cluster update (Sec. 2 steps (i)-(viii); clock: Wolff's
+ * embedded clusters, Sec. 4).  Every stage of a sweep runs as a CUDA kernel
+ * on the calling thread's current device:
+ *   bond activation  -> tile-local cluster labeling in shared memory
+ *   -> boundary merge (atomicMin union-find) -> flatten + per-cluster draw
+ *   + spin write -> integer reductions of the observables.
+ *
+ * Conventions (identical, by specification, to the CPU oracle's):
+ *   site i = y*L + x (row-major); site i owns the bond to (y, x+1 mod L)
+ *   ("right", direction 0) and to (y+1 mod L, x) ("down", direction 1).
+ *   spins are int8 states 0..q-1 (clock: angle 2*pi*k/q).
+ *   Random numbers: Philox-4x32-10, key = (seed lo32, seed hi32), counter =
+ *   (index, sweep lo32, tag, sweep hi32); tag 0 bonds (index i>>1, lane
+ *   2*(i&1)+direction), tag 1 cluster draw (index = root, lane 0), tag 2
+ *   clock mirror axis (index 0, lane 0), tag 3 random start (index i,
+ *   sweep 0, lane 0).  "sweep" counts the sweeps completed before the one
+ *   drawing.  mulhi(u, q) = (u * q) >> 32.
+ *   A bond is active iff its draw u < an integer threshold
+ *   floor(p * 2^32) (clamped to 2^32-1), p = -expm1(-x) evaluated in double:
+ *     SW_POTTS x = J/T            (Sec. 2 step (ii): p = 1 - e^{-beta})
+ *     SW_ISING x = 2J/T           (same chain in Ising units, q = 2)
+ *     SW_CLOCK x = (2J/T) * (a*b) with a, b = sin(pi*r/q), r = j mod q the
+ *              projection classes j = (2k - m) mod 2q of the two states on
+ *              the sweep's mirror axis m; zero unless both j lie strictly on
+ *              the same side (0<j<q or q<j<2q).
+ *   The label of a cluster is its smallest site index (the "proper label"
+ *   of Sec. 2); Potts clusters take state mulhi(u_root, q) (Sec. 2 steps
+ *   (v)-(vii)); clock clusters are reflected k -> (m - k) mod q iff the top
+ *   bit of u_root is set (Sec. 4).  J = 1.
+ *
+ * Counters (int64) measured after every sweep, in this order:
+ *   n_0 .. n_{q-1}     state counts of the new configuration (Eq. M^2)
+ *   class_0 .. class_{C-1}  bond classes of the new configuration
+ *                      Potts/Ising: C = 2, class 0 equal pair, 1 unequal;
+ *                      clock: C = q/2 + 1, class d = min(dk, q - dk)
+ *   active             active bonds of the sweep
+ *   clusters           clusters of the sweep
+ *
+ * Errors: every int-returning call returns SW_OK (0) or a negative status;
+ * sw_last_error() gives a thread-local message.  The library never exits or
+ * aborts.  Device-side failures (a bounded loop that ran out) are sticky per
+ * handle and reported by the next sw_sweep/sw_measure/sw_synchronize.
+ * Ownership: a handle owns its device buffers (cudaMalloc'd on the device
+ * current at sw_create) unless created with sw_create_ext, which borrows
+ * caller buffers that must outlive the handle.  Handles are not
+ * thread-safe; use one handle per thread or serialise calls.
+ */
+#ifndef SW_GB300_H
+#define SW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum sw_model { SW_POTTS = 0, SW_CLOCK = 1, SW_ISING = 2 };
+
+enum sw_status {
+    SW_OK = 0,
+    SW_ERR_ARG = -1,            /* invalid argument                        */
+    SW_ERR_OOM = -2,            /* device or host allocation failed        */
+    SW_ERR_CUDA = -3,           /* a CUDA runtime call failed              */
+    SW_ERR_NOT_CONVERGED = -4,  /* a bounded device loop ran out (sticky)  */
+    SW_ERR_STATE = -5           /* call not valid in the handle's state    */
+};
+
+enum sw_init_mode { SW_INIT_UP = 0, SW_INIT_RANDOM = 1 };
+
+#define SW_MAX_Q 127
+#define SW_MAX_CLOCK_Q 64
+#define SW_MAX_COUNTERS (SW_MAX_Q + SW_MAX_Q / 2 + 1 + 2)
+
+typedef struct sw_handle sw_handle;
+
+/* Observables after the last sweep plus running means since sw_reset_stats
+ * (Sec. 4: energy, magnetisation, moment ratio U = <M^4>/<M^2>^2, Eq. U).
+ * Per-site values: e = E/N, m2 = M^2/N^2 with M^2 from Eq. (M^2) (Potts,
+ * Ising) or |sum_i S_i|^2 (clock); absm = sqrt(m2); m4 = m2^2. */
+typedef struct sw_obs {
+    uint64_t sweep;              /* sweeps completed                          */
+    int32_t L, q, model, ncounters;
+    int64_t counts[SW_MAX_COUNTERS];   /* counters of the last sweep          */
+    double e, absm, m2, m4;      /* observables of the last sweep             */
+    uint64_t nmeas;              /* sweeps accumulated in the means below     */
+    double mean_e, mean_e2, mean_absm, mean_m2, mean_m4;
+    double binder_u;             /* mean_m4 / mean_m2^2 (Eq. U)              */
+    double mean_active, mean_clusters;
+} sw_obs;
+
+/* Number of counters per sweep for (q, model): q + C + 2. */
+int sw_ncounters(int q, int model);
+
+/* Create a lattice on the current device: 4 <= L <= 46340, L % 4 == 0;
+ * Potts 2 <= q <= 127; Ising q == 2; clock 2 <= q <= 64; T > 0 finite.
+ * Spins start all in state 0; measurement is on.  NULL on error. */
+sw_handle *sw_create(int L, int q, int model, double T, uint64_t seed);
+
+/* As sw_create, but borrow caller-owned device buffers (spins: L*L int8,
+ * labels: L*L int32, both 16-byte aligned) and run on `stream`
+ * (a cudaStream_t, NULL = legacy default stream).  Either buffer may be
+ * NULL, in which case the library allocates it. */
+sw_handle *sw_create_ext(int L, int q, int model, double T, uint64_t seed,
+                         void *d_spins, void *d_labels, void *stream);
+
+/* Release everything the handle owns (NULL-safe).  Synchronises its stream. */
+int sw_destroy(sw_handle *h);
+
+/* Thread-local description of the last failure. */
+const char *sw_last_error(void);
+
+/* (Re)initialise the spins: SW_INIT_UP (all 0) or SW_INIT_RANDOM
+ * (mulhi(u_INIT(i), q)).  Does not change the sweep index. */
+int sw_init(sw_handle *h, int mode);
+
+/* Enqueue n >= 0 sweeps on the handle's stream.  Asynchronous, except that
+ * the per-sweep counter ring (1024 sweeps) is drained to the host when full.
+ * Returns a sticky device error if one was recorded earlier. */
+int sw_sweep(sw_handle *h, int n);
+
+/* Wait for the stream, fold every pending sweep's counters into the running
+ * means, and fill *out (may be NULL just to drain). */
+int sw_measure(sw_handle *h, sw_obs *out);
+
+/* Wait for the handle's stream; report any sticky device error. */
+int sw_synchronize(sw_handle *h);
+
+/* Counters on (1, default: the paper's "+ measurement") or off (0,
+ * "update only").  Sweeps run with counters off are not accumulated. */
+int sw_set_measure(sw_handle *h, int on);
+
+/* Keep (1) or drop (0, default) the per-sweep counter rows on the host;
+ * sw_take_counts() returns and clears them. */
+int sw_set_record(sw_handle *h, int on);
+/* Copy up to max_rows recorded rows (ncounters int64 each, oldest first)
+ * into out and drop them; returns the number of rows copied (>= 0). */
+int sw_take_counts(sw_handle *h, int64_t *out, int max_rows);
+
+/* Zero the running means. */
+int sw_reset_stats(sw_handle *h);
+
+/* Write every site's canonical cluster label (smallest site index) during
+ * the sweeps that follow (1), or not (0, default). */
+int sw_set_debug_labels(sw_handle *h, int on);
+
+/* Host copies (synchronous on the handle's stream).  n must equal L*L. */
+int sw_get_spins(sw_handle *h, int8_t *host, size_t n);
+int sw_set_spins(sw_handle *h, const int8_t *host, size_t n);
+/* Labels of the last sweep; valid for sweeps run with debug labels on. */
+int sw_get_labels(sw_handle *h, int32_t *host, size_t n);
+
+/* Device pointers of the handle's buffers (for zero-copy framework use). */
+void *sw_device_spins(sw_handle *h);
+void *sw_device_labels(sw_handle *h);
+
+/* Potts/Ising: 1 threshold; clock: the (2q)^2 table, row-major by class j.
+ * Returns the number of entries written or a negative status. */
+int sw_get_thresholds(sw_handle *h, uint32_t *out, int n);
+
+/* Sweep index (sweeps completed); setting it positions the random stream
+ * (checkpoint/resume: spins + sweep index + seed + parameters). */
+int sw_get_sweep(sw_handle *h, uint64_t *out);
+int sw_set_sweep(sw_handle *h, uint64_t t);
+
+/* Use a different stream for subsequent work (a cudaStream_t). */
+int sw_set_stream(sw_handle *h, void *stream);
+
+/* Capture one sweep as a CUDA graph and replay it for every later sweep
+ * (1), or launch the kernels directly (0, default).  Same results. */
+int sw_set_graph(sw_handle *h, int on);
+
+/* Tracing: run n sweeps with CUDA events recorded on the handle's stream
+ * around every kernel (direct launches) and write the mean device time per
+ * sweep of each stage in milliseconds to ms[0 .. stages-1]:
+ *   0 bond activation + tile-local labeling (+ bond classes of the incoming
+ *     configuration), 1 merge across tile edges, 2 root flattening,
+ *   3 cluster draws + spin write (+ state counts).
+ * The sweeps count like any others.  Returns the number of stages (>0). */
+int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SW_GB300_H */

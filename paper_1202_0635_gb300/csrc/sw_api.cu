@@ -1,0 +1,653 @@
+// sw_api.cu -- host engine and C ABI of the Swendsen-Wang library.
+//
+// Owns the device state of each lattice, computes the integer bond
+// thresholds (Sec. 2 step (ii) of Komura & Okabe; clock: Sec. 4 embedding),
+// enqueues the sweep kernels (directly or as a captured CUDA graph), drains
+// the per-sweep counter ring and turns counters into FP64 observables
+// (Eq. 1, Eq. clock, Eq. M^2, Eq. U).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sw_internal.h"
+
+using swgb::DevState;
+using swgb::Lattice;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SW_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+// floor(p * 2^32) clamped to 2^32 - 1 with p = -expm1(-x) in double.
+uint32_t threshold_of(double x)
+{
+    if (!(x > 0.0)) return 0u;
+    const double p = -std::expm1(-x);
+    const double scaled = std::floor(std::ldexp(p, 32));
+    if (scaled >= 4294967295.0) return 0xffffffffu;
+    if (scaled <= 0.0) return 0u;
+    return (uint32_t)scaled;
+}
+
+int nclass_of(int q, int model) { return model == SW_CLOCK ? q / 2 + 1 : 2; }
+
+}  // namespace
+
+struct sw_handle {
+    int L = 0, q = 0, model = 0;
+    double T = 0.0;
+    uint64_t seed = 0;
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false, own_spin = false, own_label = false;
+    int8_t *d_spin = nullptr;
+    int32_t *d_label = nullptr;
+    uint32_t *d_thr_tab = nullptr;
+    uint16_t *d_code = nullptr;
+    int32_t *d_open_list = nullptr, *d_open_count = nullptr;
+    uint32_t *d_cross = nullptr;
+    int tiles_x = 0, tiles_y = 0;
+    DevState *d_st = nullptr;
+    unsigned long long *d_ring = nullptr;
+    uint32_t thr = 0;
+    std::vector<uint32_t> thr_tab;
+    int ncounters = 0, nclass = 0;
+    bool measure = true, labels = false, record = false, use_graph = false;
+    uint64_t t_host = 0;       // sweep index after all enqueued work
+    uint64_t t_drained = 0;    // first sweep whose counters are still on the device
+    int sticky = SW_OK;
+    std::string sticky_msg;
+    // host statistics
+    std::vector<int64_t> last_counts, history;
+    bool have_last = false;
+    uint64_t nmeas = 0;
+    double sum_e = 0, sum_e2 = 0, sum_absm = 0, sum_m2 = 0, sum_m4 = 0, sum_active = 0, sum_clusters = 0;
+    // captured sweep
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+
+    Lattice lattice() const
+    {
+        Lattice lat{};
+        lat.L = L;
+        lat.q = q;
+        lat.clock = model == SW_CLOCK;
+        lat.thr = thr;
+        lat.thr_tab = d_thr_tab;
+        lat.key0 = (uint32_t)(seed & 0xffffffffu);
+        lat.key1 = (uint32_t)(seed >> 32);
+        lat.spin = d_spin;
+        lat.label = d_label;
+        lat.code = d_code;
+        lat.open_list = d_open_list;
+        lat.open_count = d_open_count;
+        lat.cross = d_cross;
+        lat.tiles_x = tiles_x;
+        lat.tiles_y = tiles_y;
+        lat.st = d_st;
+        lat.ring = d_ring;
+        lat.ring_slots = swgb::kRingSlots;
+        lat.ncounters = ncounters;
+        lat.nclass = nclass;
+        return lat;
+    }
+};
+
+namespace {
+
+void drop_graph(sw_handle *h)
+{
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+}
+
+// Observables of one counter row (Sec. 4 measurement):
+//   Potts E = number of unequal pairs (Eq. 1, J = 1); Ising E = -(equal - unequal);
+//   clock E = -sum_d class_d cos(2 pi d / q);
+//   Potts/Ising M^2 = (q sum n_k^2 - N^2)/(q - 1) (Eq. M^2), numerator exact;
+//   clock M^2 = |sum_k n_k (cos, sin)(2 pi k / q)|^2.
+void observables_of(int L, int q, int model, const int64_t *c, double out[4])
+{
+    const int64_t N = (int64_t)L * L;
+    const double dN = (double)N;
+    double E, M2;
+    if (model == SW_CLOCK) {
+        const int nclass = q / 2 + 1;
+        E = 0.0;
+        for (int d = 0; d < nclass; ++d) E -= (double)c[q + d] * std::cos(2.0 * M_PI * (double)d / (double)q);
+        double mx = 0.0, my = 0.0;
+        for (int k = 0; k < q; ++k) {
+            mx += (double)c[k] * std::cos(2.0 * M_PI * (double)k / (double)q);
+            my += (double)c[k] * std::sin(2.0 * M_PI * (double)k / (double)q);
+        }
+        M2 = mx * mx + my * my;
+    } else {
+        E = model == SW_ISING ? -(double)(c[q] - c[q + 1]) : (double)c[q + 1];
+        __int128 s2 = 0;
+        for (int k = 0; k < q; ++k) s2 += (__int128)c[k] * (__int128)c[k];
+        const __int128 num = (__int128)q * s2 - (__int128)N * (__int128)N;
+        M2 = (double)num / (double)(q - 1);
+    }
+    const double m2 = M2 / (dN * dN);
+    out[0] = E / dN;
+    out[1] = std::sqrt(M2) / dN;
+    out[2] = m2;
+    out[3] = m2 * m2;
+}
+
+void accumulate(sw_handle *h, const int64_t *row)
+{
+    double o[4];
+    observables_of(h->L, h->q, h->model, row, o);
+    h->nmeas++;
+    h->sum_e += o[0];
+    h->sum_e2 += o[0] * o[0];
+    h->sum_absm += o[1];
+    h->sum_m2 += o[2];
+    h->sum_m4 += o[3];
+    h->sum_active += (double)row[h->q + h->nclass];
+    h->sum_clusters += (double)row[h->q + h->nclass + 1];
+    h->last_counts.assign(row, row + h->ncounters);
+    h->have_last = true;
+    if (h->record) h->history.insert(h->history.end(), row, row + h->ncounters);
+}
+
+int check_device_error(sw_handle *h)
+{
+    DevState st;
+    SW_CUDA(cudaMemcpyAsync(&st, h->d_st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    if (st.err != swgb::kErrNone && h->sticky == SW_OK) {
+        h->sticky = SW_ERR_NOT_CONVERGED;
+        char buf[160];
+        snprintf(buf, sizeof buf, "device loop bound exceeded (code %d at index %d)", st.err, st.err_where);
+        h->sticky_msg = buf;
+    }
+    if (h->sticky != SW_OK) return fail(h->sticky, "%s", h->sticky_msg.c_str());
+    return SW_OK;
+}
+
+// Wait for the stream and fold every pending measured sweep into the host
+// statistics, oldest first.
+int drain(sw_handle *h)
+{
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    const uint64_t pending = h->t_host - h->t_drained;
+    if (pending > 0 && h->measure) {
+        // The bond classes of the newest configuration are normally counted
+        // by the next sweep's labeling pass; count them now.
+        cudaError_t e = swgb::launch_pending_classes(h->lattice(), h->sm_count, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launch_pending_classes");
+        SW_CUDA(cudaStreamSynchronize(h->stream));
+        std::vector<unsigned long long> rows((size_t)swgb::kRingSlots * h->ncounters);
+        SW_CUDA(cudaMemcpy(rows.data(), h->d_ring, rows.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost));
+        std::vector<int64_t> row(h->ncounters);
+        for (uint64_t t = h->t_drained; t < h->t_host; ++t) {
+            const size_t slot = (size_t)(t % swgb::kRingSlots);
+            for (int c = 0; c < h->ncounters; ++c) row[c] = (int64_t)rows[slot * h->ncounters + c];
+            accumulate(h, row.data());
+        }
+    }
+    h->t_drained = h->t_host;
+    return check_device_error(h);
+}
+
+int reset_device_index(sw_handle *h, uint64_t t)
+{
+    DevState st{};
+    st.sweep = t;
+    st.classes_upto = t;   // the current configuration is not a sweep result of this run
+    SW_CUDA(cudaMemcpyAsync(h->d_st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+    SW_CUDA(cudaMemsetAsync(h->d_ring, 0, sizeof(unsigned long long) * swgb::kRingSlots * h->ncounters, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    h->t_host = h->t_drained = t;
+    h->sticky = SW_OK;
+    return SW_OK;
+}
+
+int enqueue_one(sw_handle *h)
+{
+    if (h->use_graph) {
+        if (!h->graph_exec) {
+            SW_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t le = swgb::launch_sweep(h->lattice(), h->measure, h->labels, h->sm_count, h->stream);
+            cudaError_t ce = cudaStreamEndCapture(h->stream, &h->graph);
+            if (le != cudaSuccess) return cuda_fail(le, "launch_sweep (capture)");
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+            SW_CUDA(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+        }
+        SW_CUDA(cudaGraphLaunch(h->graph_exec, h->stream));
+        return SW_OK;
+    }
+    cudaError_t e = swgb::launch_sweep(h->lattice(), h->measure, h->labels, h->sm_count, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_sweep");
+    return SW_OK;
+}
+
+void free_handle(sw_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    if (h->own_spin && h->d_spin) cudaFree(h->d_spin);
+    if (h->own_label && h->d_label) cudaFree(h->d_label);
+    if (h->d_thr_tab) cudaFree(h->d_thr_tab);
+    if (h->d_code) cudaFree(h->d_code);
+    if (h->d_open_list) cudaFree(h->d_open_list);
+    if (h->d_open_count) cudaFree(h->d_open_count);
+    if (h->d_cross) cudaFree(h->d_cross);
+    if (h->d_st) cudaFree(h->d_st);
+    if (h->d_ring) cudaFree(h->d_ring);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int validate(int L, int q, int model, double T)
+{
+    if (model != SW_POTTS && model != SW_CLOCK && model != SW_ISING)
+        return fail(SW_ERR_ARG, "unknown model %d", model);
+    if (L < 4 || L % 4 != 0 || L > 46340)
+        return fail(SW_ERR_ARG, "L=%d: need 4 <= L <= 46340 and L %% 4 == 0", L);
+    if (model == SW_ISING && q != 2) return fail(SW_ERR_ARG, "Ising needs q = 2 (got %d)", q);
+    if (q < 2 || q > SW_MAX_Q) return fail(SW_ERR_ARG, "q=%d out of [2, %d]", q, SW_MAX_Q);
+    if (model == SW_CLOCK && q > SW_MAX_CLOCK_Q) return fail(SW_ERR_ARG, "clock q=%d > %d", q, SW_MAX_CLOCK_Q);
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(SW_ERR_ARG, "T=%g must be positive and finite", T);
+    return SW_OK;
+}
+
+sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d_spins, void *d_labels,
+                       void *stream, bool have_stream)
+{
+    if (validate(L, q, model, T) != SW_OK) return nullptr;
+    if ((d_spins && ((uintptr_t)d_spins & 15)) || (d_labels && ((uintptr_t)d_labels & 15))) {
+        fail(SW_ERR_ARG, "borrowed buffers must be 16-byte aligned");
+        return nullptr;
+    }
+    sw_handle *h = new (std::nothrow) sw_handle();
+    if (!h) {
+        fail(SW_ERR_OOM, "host allocation failed");
+        return nullptr;
+    }
+    h->L = L;
+    h->q = q;
+    h->model = model;
+    h->T = T;
+    h->seed = seed;
+    h->nclass = nclass_of(q, model);
+    h->ncounters = q + h->nclass + 2;
+    const size_t N = (size_t)L * L;
+    auto bail = [&](cudaError_t e, const char *what) -> sw_handle * {
+        cuda_fail(e, what);
+        free_handle(h);
+        return nullptr;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+        return bail(e, "cudaDeviceGetAttribute");
+    if (have_stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e, "cudaStreamCreate");
+        h->own_stream = true;
+    }
+    if (d_spins) {
+        h->d_spin = (int8_t *)d_spins;
+    } else {
+        if ((e = cudaMalloc(&h->d_spin, N)) != cudaSuccess) return bail(e, "cudaMalloc(spins)");
+        h->own_spin = true;
+    }
+    if (d_labels) {
+        h->d_label = (int32_t *)d_labels;
+    } else {
+        if ((e = cudaMalloc(&h->d_label, N * sizeof(int32_t))) != cudaSuccess) return bail(e, "cudaMalloc(labels)");
+        h->own_label = true;
+    }
+    if ((e = cudaMalloc(&h->d_st, sizeof(DevState))) != cudaSuccess) return bail(e, "cudaMalloc(state)");
+    h->tiles_x = (L + swgb::kTileW - 1) / swgb::kTileW;
+    h->tiles_y = (L + swgb::kTileH - 1) / swgb::kTileH;
+    const size_t ntiles = (size_t)h->tiles_x * h->tiles_y;
+    if ((e = cudaMalloc(&h->d_code, N * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(codes)");
+    if ((e = cudaMalloc(&h->d_open_list, ntiles * swgb::kOpenSlots * sizeof(int32_t))) != cudaSuccess)
+        return bail(e, "cudaMalloc(open roots)");
+    if ((e = cudaMalloc(&h->d_open_count, ntiles * sizeof(int32_t))) != cudaSuccess)
+        return bail(e, "cudaMalloc(open counts)");
+    if ((e = cudaMalloc(&h->d_cross, ntiles * swgb::kCrossWords * sizeof(uint32_t))) != cudaSuccess)
+        return bail(e, "cudaMalloc(crossing bonds)");
+    if ((e = cudaMalloc(&h->d_ring, sizeof(unsigned long long) * swgb::kRingSlots * h->ncounters)) != cudaSuccess)
+        return bail(e, "cudaMalloc(ring)");
+
+    // Bond thresholds (Sec. 2 step (ii); clock: Sec. 4 embedding), J = 1.
+    const double K = 1.0 / T;
+    if (model == SW_POTTS) {
+        h->thr = threshold_of(K);
+    } else if (model == SW_ISING) {
+        h->thr = threshold_of(2.0 * K);
+    } else {
+        const int n2 = 2 * q;
+        h->thr_tab.assign((size_t)n2 * n2, 0u);
+        for (int a = 0; a < n2; ++a) {
+            for (int b = 0; b < n2; ++b) {
+                const int side_a = (a % q == 0) ? 0 : (a < q ? 1 : -1);
+                const int side_b = (b % q == 0) ? 0 : (b < q ? 1 : -1);
+                if (side_a == 0 || side_a != side_b) continue;
+                const double pa = std::sin((M_PI * (double)(a % q)) / (double)q);
+                const double pb = std::sin((M_PI * (double)(b % q)) / (double)q);
+                h->thr_tab[(size_t)a * n2 + b] = threshold_of((2.0 * K) * (pa * pb));
+            }
+        }
+        if ((e = cudaMalloc(&h->d_thr_tab, h->thr_tab.size() * sizeof(uint32_t))) != cudaSuccess)
+            return bail(e, "cudaMalloc(thresholds)");
+        if ((e = cudaMemcpy(h->d_thr_tab, h->thr_tab.data(), h->thr_tab.size() * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy(thresholds)");
+    }
+    if (reset_device_index(h, 0) != SW_OK) {
+        free_handle(h);
+        return nullptr;
+    }
+    if ((e = cudaMemsetAsync(h->d_spin, 0, N, h->stream)) != cudaSuccess) return bail(e, "cudaMemset(spins)");
+    if ((e = cudaMemsetAsync(h->d_label, 0, N * sizeof(int32_t), h->stream)) != cudaSuccess)
+        return bail(e, "cudaMemset(labels)");
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "cudaStreamSynchronize");
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sw_ncounters(int q, int model) { return q + nclass_of(q, model) + 2; }
+
+const char *sw_last_error(void) { return g_err.c_str(); }
+
+sw_handle *sw_create(int L, int q, int model, double T, uint64_t seed)
+{
+    return create_impl(L, q, model, T, seed, nullptr, nullptr, nullptr, false);
+}
+
+sw_handle *sw_create_ext(int L, int q, int model, double T, uint64_t seed, void *d_spins, void *d_labels,
+                         void *stream)
+{
+    return create_impl(L, q, model, T, seed, d_spins, d_labels, stream, true);
+}
+
+int sw_destroy(sw_handle *h)
+{
+    free_handle(h);
+    return SW_OK;
+}
+
+int sw_init(sw_handle *h, int mode)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (mode != SW_INIT_UP && mode != SW_INIT_RANDOM) return fail(SW_ERR_ARG, "unknown init mode %d", mode);
+    cudaError_t e = swgb::launch_init(h->lattice(), mode == SW_INIT_RANDOM, h->sm_count, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_init");
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    return SW_OK;
+}
+
+int sw_sweep(sw_handle *h, int n)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (n < 0) return fail(SW_ERR_ARG, "n=%d < 0", n);
+    if (h->sticky != SW_OK) return fail(h->sticky, "%s", h->sticky_msg.c_str());
+    for (int s = 0; s < n; ++s) {
+        if (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) {
+            int rc = drain(h);
+            if (rc != SW_OK) return rc;
+        }
+        int rc = enqueue_one(h);
+        if (rc != SW_OK) return rc;
+        h->t_host++;
+        if (!h->measure) h->t_drained = h->t_host;
+    }
+    return SW_OK;
+}
+
+int sw_synchronize(sw_handle *h)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    return check_device_error(h);
+}
+
+int sw_measure(sw_handle *h, sw_obs *out)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    if (!out) return SW_OK;
+    std::memset(out, 0, sizeof *out);
+    out->sweep = h->t_host;
+    out->L = h->L;
+    out->q = h->q;
+    out->model = h->model;
+    out->ncounters = h->ncounters;
+    if (h->have_last) {
+        for (int c = 0; c < h->ncounters; ++c) out->counts[c] = h->last_counts[c];
+        double o[4];
+        observables_of(h->L, h->q, h->model, h->last_counts.data(), o);
+        out->e = o[0];
+        out->absm = o[1];
+        out->m2 = o[2];
+        out->m4 = o[3];
+    }
+    out->nmeas = h->nmeas;
+    if (h->nmeas) {
+        const double n = (double)h->nmeas;
+        out->mean_e = h->sum_e / n;
+        out->mean_e2 = h->sum_e2 / n;
+        out->mean_absm = h->sum_absm / n;
+        out->mean_m2 = h->sum_m2 / n;
+        out->mean_m4 = h->sum_m4 / n;
+        out->binder_u = out->mean_m2 > 0 ? out->mean_m4 / (out->mean_m2 * out->mean_m2) : 0.0;
+        out->mean_active = h->sum_active / n;
+        out->mean_clusters = h->sum_clusters / n;
+    }
+    return SW_OK;
+}
+
+int sw_set_measure(sw_handle *h, int on)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    if (h->measure != (on != 0)) drop_graph(h);
+    h->measure = on != 0;
+    return SW_OK;
+}
+
+int sw_set_record(sw_handle *h, int on)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    h->record = on != 0;
+    if (!h->record) h->history.clear();
+    return SW_OK;
+}
+
+int sw_take_counts(sw_handle *h, int64_t *out, int max_rows)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (max_rows < 0 || (max_rows > 0 && !out)) return fail(SW_ERR_ARG, "bad output buffer");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    const size_t have = h->history.size() / h->ncounters;
+    const size_t n = std::min(have, (size_t)max_rows);
+    std::memcpy(out, h->history.data(), n * h->ncounters * sizeof(int64_t));
+    h->history.erase(h->history.begin(), h->history.begin() + n * h->ncounters);
+    return (int)n;
+}
+
+int sw_reset_stats(sw_handle *h)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    h->nmeas = 0;
+    h->sum_e = h->sum_e2 = h->sum_absm = h->sum_m2 = h->sum_m4 = h->sum_active = h->sum_clusters = 0.0;
+    return SW_OK;
+}
+
+int sw_set_debug_labels(sw_handle *h, int on)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (h->labels != (on != 0)) drop_graph(h);
+    h->labels = on != 0;
+    return SW_OK;
+}
+
+int sw_get_spins(sw_handle *h, int8_t *host, size_t n)
+{
+    if (!h || !host) return fail(SW_ERR_ARG, "null argument");
+    if (n != (size_t)h->L * h->L) return fail(SW_ERR_ARG, "n=%zu != L*L", n);
+    SW_CUDA(cudaMemcpyAsync(host, h->d_spin, n, cudaMemcpyDeviceToHost, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    return SW_OK;
+}
+
+int sw_set_spins(sw_handle *h, const int8_t *host, size_t n)
+{
+    if (!h || !host) return fail(SW_ERR_ARG, "null argument");
+    if (n != (size_t)h->L * h->L) return fail(SW_ERR_ARG, "n=%zu != L*L", n);
+    for (size_t i = 0; i < n; ++i)
+        if (host[i] < 0 || host[i] >= h->q) return fail(SW_ERR_ARG, "spin %zu = %d outside [0, q)", i, host[i]);
+    SW_CUDA(cudaMemcpyAsync(h->d_spin, host, n, cudaMemcpyHostToDevice, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    return SW_OK;
+}
+
+int sw_get_labels(sw_handle *h, int32_t *host, size_t n)
+{
+    if (!h || !host) return fail(SW_ERR_ARG, "null argument");
+    if (n != (size_t)h->L * h->L) return fail(SW_ERR_ARG, "n=%zu != L*L", n);
+    SW_CUDA(cudaMemcpyAsync(host, h->d_label, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    return SW_OK;
+}
+
+void *sw_device_spins(sw_handle *h) { return h ? (void *)h->d_spin : nullptr; }
+void *sw_device_labels(sw_handle *h) { return h ? (void *)h->d_label : nullptr; }
+
+int sw_get_thresholds(sw_handle *h, uint32_t *out, int n)
+{
+    if (!h || !out) return fail(SW_ERR_ARG, "null argument");
+    if (h->model == SW_CLOCK) {
+        const int m = (int)h->thr_tab.size();
+        if (n < m) return fail(SW_ERR_ARG, "need %d entries", m);
+        std::memcpy(out, h->thr_tab.data(), (size_t)m * sizeof(uint32_t));
+        return m;
+    }
+    if (n < 1) return fail(SW_ERR_ARG, "need 1 entry");
+    out[0] = h->thr;
+    return 1;
+}
+
+int sw_get_sweep(sw_handle *h, uint64_t *out)
+{
+    if (!h || !out) return fail(SW_ERR_ARG, "null argument");
+    *out = h->t_host;
+    return SW_OK;
+}
+
+int sw_set_sweep(sw_handle *h, uint64_t t)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    return reset_device_index(h, t);
+}
+
+int sw_set_stream(sw_handle *h, void *stream)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    h->own_stream = false;
+    h->stream = (cudaStream_t)stream;
+    drop_graph(h);
+    return SW_OK;
+}
+
+int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages)
+{
+    if (!h || !ms) return fail(SW_ERR_ARG, "null argument");
+    if (n < 1 || max_stages < 1) return fail(SW_ERR_ARG, "n and max_stages must be positive");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    const int nstages = swgb::kMaxStages;
+    cudaEvent_t ev[swgb::kMaxStages + 1];
+    for (int k = 0; k <= nstages; ++k) SW_CUDA(cudaEventCreate(&ev[k]));
+    std::vector<double> acc(nstages, 0.0);
+    for (int s = 0; s < n && rc == SW_OK; ++s) {
+        if (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) rc = drain(h);
+        if (rc != SW_OK) break;
+        cudaError_t e = swgb::launch_sweep(h->lattice(), h->measure, h->labels, h->sm_count, h->stream, ev);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "launch_sweep");
+            break;
+        }
+        h->t_host++;
+        if (!h->measure) h->t_drained = h->t_host;
+        e = cudaEventSynchronize(ev[nstages]);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaEventSynchronize");
+            break;
+        }
+        for (int k = 0; k < nstages; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (int k = 0; k <= nstages; ++k) cudaEventDestroy(ev[k]);
+    if (rc != SW_OK) return rc;
+    const int m = std::min(nstages, max_stages);
+    for (int k = 0; k < m; ++k) ms[k] = (float)(acc[k] / n);
+    rc = drain(h);
+    return rc != SW_OK ? rc : m;
+}
+
+int sw_set_graph(sw_handle *h, int on)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (h->use_graph != (on != 0)) drop_graph(h);
+    h->use_graph = on != 0;
+    return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+// sw_device.cuh -- device-side building blocks of the Swendsen-Wang sweep:
+// the counter-based generator, the kernel parameter block and the bounded
+// union-find primitives.  Written for sm_103a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swgb {
+
+// Random-number tags of the counter (index, sweep lo, tag, sweep hi).
+enum : uint32_t { kTagBond = 0, kTagState = 1, kTagAxis = 2, kTagInit = 3 };
+
+// Error codes stored in the device state word (first error wins).
+enum : int { kErrNone = 0, kErrFindCap = 1, kErrUnionCap = 2, kErrTimeBudget = 3, kErrInternal = 4 };
+
+// Wall-clock budget of any single data-dependent device loop (~1 s at the
+// GB300's 2.07 GHz maximum SM clock).  A loop that exceeds it records an
+// error and returns instead of spinning on.
+constexpr long long kLoopBudgetCycles = 2000000000ll;
+
+// Sticky per-lattice device state.
+struct DevState {
+    unsigned long long sweep;          // sweeps completed; read by every kernel of a sweep
+    unsigned long long classes_upto;   // configurations < this index have their bond classes counted
+    unsigned int ticket;               // blocks finished in the sweep's last kernel
+    int err;                           // first device error (kErr*)
+    int err_where;                     // site or index that hit it
+    int pad;
+};
+
+// Everything a kernel needs about one lattice.  Passed by value.
+struct Lattice {
+    int L;                      // linear size (L % 4 == 0)
+    int q;                      // number of states
+    int clock;                  // 1: clock model, 0: Potts / Ising
+    uint32_t thr;               // Potts / Ising bond threshold
+    const uint32_t *thr_tab;    // clock: (2q) x (2q) thresholds by class
+    uint32_t key0, key1;        // Philox key = seed
+    int8_t *spin;               // L*L states
+    int32_t *label;             // L*L words: union-find parents of open tile roots; debug labels
+    uint16_t *code;             // L*L per-site codes written by the labeling stage
+    int32_t *open_list;         // tiles x kOpenSlots global indices of open tile roots
+    int32_t *open_count;        // tiles
+    uint32_t *cross;            // tiles x 2 words: active crossing bonds (right edge rows, bottom edge columns)
+    int tiles_x, tiles_y;
+    DevState *st;
+    unsigned long long *ring;   // ring_slots x ncounters counters
+    int ring_slots;
+    int ncounters;
+    int nclass;
+};
+
+// Philox-4x32-10 (Salmon et al., SC'11).  Each round takes two 32x32->64
+// products; their high halves are mixed with the other two words and the
+// round key, and the key advances by the two Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw4(const Lattice &lat, uint32_t index, unsigned long long t, uint32_t tag)
+{
+    return philox4x32_10(make_uint4(index, (uint32_t)t, tag, (uint32_t)(t >> 32)), lat.key0, lat.key1);
+}
+
+__device__ __forceinline__ int mulhi_q(uint32_t u, int q)
+{
+    return (int)__umulhi(u, (uint32_t)q);
+}
+
+// Mirror axis of the sweep (clock model).
+__device__ __forceinline__ int clock_axis(const Lattice &lat, unsigned long long t)
+{
+    return mulhi_q(draw4(lat, 0u, t, kTagAxis).x, lat.q);
+}
+
+// Projection class j = (2k - m) mod 2q.
+__device__ __forceinline__ int clock_class(int k, int m, int q)
+{
+    int j = 2 * k - m;
+    return j < 0 ? j + 2 * q : j;
+}
+
+__device__ __forceinline__ void record_error(DevState *st, int code, int where)
+{
+    if (atomicCAS(&st->err, kErrNone, code) == kErrNone) st->err_where = where;
+}
+
+// ---------------------------------------------------------------------------
+// Global union-find over the label array.  Invariant: label[x] <= x, so the
+// root of every tree is its smallest element and chains strictly decrease
+// (a chase can never exceed the number of sites).  Roots are linked larger
+// under smaller with atomicMin; path halving writes only ancestors.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_volatile(const int32_t *p)
+{
+    return *reinterpret_cast<const volatile int32_t *>(p);
+}
+
+__device__ __forceinline__ int find_root_halving(int32_t *label, int x, int cap, DevState *st)
+{
+    const long long t0 = clock64();
+    for (int it = 0; it < cap; ++it) {
+        const int p = ld_volatile(label + x);
+        if (p == x) return x;
+        const int gp = ld_volatile(label + p);
+        if (gp == p) return p;
+        label[x] = gp;   // ancestor of x: safe under concurrent linking
+        x = gp;
+        if ((it & 255) == 255 && clock64() - t0 > kLoopBudgetCycles) {
+            record_error(st, kErrTimeBudget, x);
+            return x;
+        }
+    }
+    record_error(st, kErrFindCap, x);
+    return x;
+}
+
+__device__ __forceinline__ void union_roots(int32_t *label, int a, int b, int cap, DevState *st)
+{
+    const long long t0 = clock64();
+    for (int it = 0; it < cap; ++it) {
+        a = find_root_halving(label, a, cap, st);
+        b = find_root_halving(label, b, cap, st);
+        if (a == b) return;
+        const int hi = a > b ? a : b;
+        const int lo = a > b ? b : a;
+        const int old = atomicMin(label + hi, lo);
+        if (old == hi) return;          // hi was a root: now under lo
+        a = old;                        // hi had moved under old: join old and lo
+        b = lo;
+        if (clock64() - t0 > kLoopBudgetCycles) {
+            record_error(st, kErrTimeBudget, a);
+            return;
+        }
+    }
+    record_error(st, kErrUnionCap, a);
+}
+
+// Read-only root chase (no concurrent writers).
+__device__ __forceinline__ int find_root_ro(const int32_t *__restrict__ label, int x, int cap, DevState *st)
+{
+    const long long t0 = clock64();
+    for (int it = 0; it < cap; ++it) {
+        const int p = __ldg(label + x);
+        if (p == x) return x;
+        x = p;
+        if ((it & 255) == 255 && clock64() - t0 > kLoopBudgetCycles) {
+            record_error(st, kErrTimeBudget, x);
+            return x;
+        }
+    }
+    record_error(st, kErrFindCap, x);
+    return x;
+}
+
+// A state outside [0, q) (only possible through a caller writing the spin
+// buffer directly) is read as state 0 wherever it would index a table.
+__device__ __forceinline__ int valid_state(int s, int q)
+{
+    return (unsigned)s < (unsigned)q ? s : 0;
+}
+
+// Shared-memory union-find on tile-local indices (same invariants).
+__device__ __forceinline__ int find_s(volatile int *par, int x, int cap)
+{
+    for (int it = 0; it < cap; ++it) {
+        const int p = par[x];
+        if (p == x) return x;
+        const int gp = par[p];
+        if (gp == p) return p;
+        par[x] = gp;
+        x = gp;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ bool union_s(volatile int *par, int a, int b, int cap)
+{
+    for (int it = 0; it < cap; ++it) {
+        a = find_s(par, a, cap);
+        b = find_s(par, b, cap);
+        if (a < 0 || b < 0) return false;
+        if (a == b) return true;
+        const int hi = a > b ? a : b;
+        const int lo = a > b ? b : a;
+        const int old = atomicMin((int *)&par[hi], lo);
+        if (old == hi) return true;
+        a = old;
+        b = lo;
+    }
+    return false;
+}
+
+// Block-wide sum of a per-thread value into one global 64-bit counter.
+template <int NT>
+__device__ __forceinline__ void block_add(unsigned long long *dst, unsigned int v, unsigned int *scratch)
+{
+    v = __reduce_add_sync(0xffffffffu, v);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;   // blocks may be 2-D
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned int s = (lane < NT / 32) ? scratch[lane] : 0u;
+        s = __reduce_add_sync(0xffffffffu, s);
+        if (lane == 0 && s) atomicAdd(dst, (unsigned long long)s);
+    }
+    __syncthreads();
+}
+
+}  // namespace swgb
