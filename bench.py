@@ -1,0 +1,339 @@
+"""Benchmark of the Swendsen-Wang sweep on GB300.
+
+Workload (one "step" = one full sweep, all stages, measurement on): the
+q = 2 Potts (Ising) model on a periodic 4096 x 4096 lattice at the critical
+temperature T_c = 1/ln(1 + sqrt 2) (Komura & Okabe, arXiv:1202.0635,
+Sec. 4, Table 1), random start followed by 200 untimed equilibration
+sweeps.  The metric is nanoseconds per spin flip (sweep time / L^2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  With N > 1 (torchrun) every rank
+advances its own independent lattice (replicas; no collective on the data
+path) and the time is the maximum over ranks.  --impl reference times the
+CPU oracle (test infrastructure) on the same workload, on rank 0 only.
+"""
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ns per spin flip at L=4096, T=Tc (frac. of HBM roofline); batched vs plain sweeps/s"
+UNIT = "ns/flip"
+L_BENCH = 4096
+Q_BENCH = 2
+T_BENCH = 1.0 / math.log(1.0 + math.sqrt(2.0))
+EQUIL_SWEEPS = 200
+L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
+
+# Algorithmic bytes per site of each stage (q = 2 Potts, measurement on):
+# the labeling stage reads the int8 spin and writes a 2-byte code, the
+# flip stage reads the code and writes the int8 spin.  The merge and
+# flattening stages touch only tile-border data.
+STAGES = ["label", "merge", "flatten", "flip"]
+ALG_BYTES_PER_SITE = {"label": 3.0, "merge": None, "flatten": None, "flip": 3.0}
+# Whole-sweep byte model of the method (int8 spins, int32 labels
+# materialised): spin read + label write + label read + spin write.
+SWEEP_BYTES_PER_SITE = 10.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_ns_per_flip(L, sweeps):
+    """Time the CPU oracle (as it stands) on an L x L lattice: random start,
+    then `sweeps` timed sweeps.  Returns (ns per flip, wall seconds)."""
+    from oracle import Oracle, POTTS
+    o = Oracle(L, Q_BENCH, POTTS, T_BENCH, 1, init="random")
+    o.sweep(1)
+    t0 = time.perf_counter()
+    o.sweep(sweeps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return dt * 1e9 / (sweeps * L * L), dt
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    total = args.steps + args.warmup
+    L = L_BENCH if total <= 30 else (2048 if total <= 120 else 1024)
+    from oracle import Oracle, POTTS
+    o = Oracle(L, Q_BENCH, POTTS, T_BENCH, 1, init="random")
+    o.sweep(args.warmup)
+    t0 = time.perf_counter()
+    o.sweep(args.steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    ns = dt * 1e9 / (args.steps * L * L)
+    sample = "%d oracle sweeps of a %dx%d lattice (q=2 Potts, T_c, random start, %d warm-up sweeps)" % (
+        args.steps, L, L, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": ns, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "q=2 Potts L=%d T=Tc random start (CPU oracle, single thread)" % L,
+                       "L": L, "q": Q_BENCH, "T": T_BENCH},
+            "cpu_baseline": {"value": ns, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ns, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1202_0635_gb300 as sw
+    from paper_1202_0635_gb300 import build as sw_build
+
+    if rank == 0 or not os.path.exists(sw_build.LIB):
+        sw_build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        dist.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    L = L_BENCH
+    N = L * L
+    lat = sw.Lattice(L, Q_BENCH, sw.SW_POTTS, T_BENCH, 1 + rank, init=sw.SW_INIT_RANDOM,
+                     stream=stream.cuda_stream)
+    sw.sw_set_graph(lat.h, 1)
+    lat.sweep(EQUIL_SWEEPS)
+    sw.sw_reset_stats(lat.h)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.add_(1)
+
+    for _ in range(args.warmup):
+        flush_l2()
+        lat.sweep(1)
+    sw.sw_synchronize(lat.h)
+
+    # ---- timed region: K sweeps, L2 flushed before each, CUDA events on the lattice stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush_l2()
+            starts[k].record(stream)
+            lat.sweep(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    obs = lat.measure()
+    ms_per_step = total_ms / args.steps
+    value = total_ms * 1e6 / (args.steps * world * N)
+
+    # ---- per-stage device times (CUDA events around each kernel, same stream)
+    prof = [0.0] * len(STAGES)
+    nprof = max(5, min(args.steps, 40))
+    for _ in range(nprof):
+        flush_l2()
+        ms = sw.sw_profile_sweeps(lat.h, 1)
+        for i, v in enumerate(ms[: len(STAGES)]):
+            prof[i] += v / nprof
+    stage_us = {name: prof[i] * 1e3 for i, name in enumerate(STAGES)}
+    dom = max(range(len(STAGES)), key=lambda i: prof[i])
+    peak, peak_kind = measured_peaks()
+    dom_name = STAGES[dom]
+    dom_bytes = ALG_BYTES_PER_SITE[dom_name]
+    achieved = (dom_bytes * N) / (prof[dom] * 1e-3) / 1e9 if dom_bytes else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(dom_name)
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_source": peak_kind, "bytes_per_site": dom_bytes}
+    sweep_roofline = {"bytes_per_site": SWEEP_BYTES_PER_SITE,
+                      "achieved": SWEEP_BYTES_PER_SITE * N / (ms_per_step * 1e-3) / 1e9,
+                      "peak": peak, "unit": "GB/s"}
+    sweep_roofline["frac"] = sweep_roofline["achieved"] / peak
+
+    # ---- update-only timing (the paper's other row), same procedure
+    sw.sw_set_measure(lat.h, 0)
+    upd = []
+    for k in range(min(args.steps, 50)):
+        flush_l2()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.sweep(1)
+        b.record(stream)
+        upd.append((a, b))
+    torch.cuda.synchronize(dev)
+    update_only = sum(a.elapsed_time(b) for a, b in upd) * 1e6 / (len(upd) * N)
+    sw.sw_set_measure(lat.h, 1)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    pinned_in = torch.empty(N, dtype=torch.int8).pin_memory()
+    pinned_in.copy_(torch.from_numpy(lat.spins.reshape(-1)))
+    host_ptr = ctypes.cast(pinned_in.data_ptr(), ctypes.POINTER(ctypes.c_int8))
+    libh = sw.lib()
+    o = sw.sw_obs()
+    ne2e = max(5, min(args.steps, 50))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        rc = libh.sw_set_spins(lat.h, host_ptr, N)
+        rc = rc or libh.sw_sweep(lat.h, 1)
+        rc = rc or libh.sw_measure(lat.h, ctypes.byref(o))
+        if rc:
+            raise RuntimeError(sw.sw_last_error())
+    e2e_s = time.perf_counter() - t0
+    e2e_value = e2e_s * 1e9 / (ne2e * N)
+    d2h = 8 * sw.sw_ncounters(Q_BENCH, sw.SW_POTTS) + 40   # counter row + device state word block
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        L_cpu, sweeps_cpu = 4096, 3
+        ns_cpu, dt_cpu = cpu_oracle_ns_per_flip(L_cpu, sweeps_cpu)
+        cpu = {"value": ns_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d sweeps of the %dx%d q=2 Potts lattice at T_c after a random start (%.1f s)" % (
+                   sweeps_cpu, L_cpu, L_cpu, dt_cpu)}
+
+    clocks = clk.summary()
+    lat.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "q=2 Potts (Ising) L=4096 periodic, T=Tc=1/ln(1+sqrt2), random start + %d "
+                               "equilibration sweeps; one sweep per step, measurement on, CUDA graph" % EQUIL_SWEEPS,
+                   "L": L, "q": Q_BENCH, "T": T_BENCH, "l2": "flushed before every timed sweep (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single lattice"},
+        "roofline": roofline,
+        "sweep_roofline": sweep_roofline,
+        "stage_us": stage_us,
+        "update_only_ns_per_flip": update_only,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "observables": {"mean_e": obs.mean_e, "binder_u": obs.binder_u, "nmeas": int(obs.nmeas)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -150,7 +150,9 @@ int sw_reset_stats(sw_handle *h);
  * the sweeps that follow (1), or not (0, default). */
 int sw_set_debug_labels(sw_handle *h, int on);
 
-/* Host copies (synchronous on the handle's stream).  n must equal L*L. */
+/* Host copies (synchronous on the handle's stream).  n must equal L*L.
+ * sw_set_spins checks every state on the device; if any lies outside
+ * [0, q) it returns SW_ERR_ARG and leaves all spins in state 0. */
 int sw_get_spins(sw_handle *h, int8_t *host, size_t n);
 int sw_set_spins(sw_handle *h, const int8_t *host, size_t n);
 /* Labels of the last sweep; valid for sweeps run with debug labels on. */

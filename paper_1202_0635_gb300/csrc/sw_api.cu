@@ -206,14 +206,20 @@ int drain(sw_handle *h)
         // by the next sweep's labeling pass; count them now.
         cudaError_t e = swgb::launch_pending_classes(h->lattice(), h->sm_count, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launch_pending_classes");
+        // Copy only the pending rows (at most two contiguous ring segments).
+        const size_t nc = (size_t)h->ncounters;
+        std::vector<unsigned long long> rows((size_t)pending * nc);
+        const size_t first = (size_t)(h->t_drained % swgb::kRingSlots);
+        const size_t n1 = std::min((size_t)pending, (size_t)swgb::kRingSlots - first);
+        SW_CUDA(cudaMemcpyAsync(rows.data(), h->d_ring + first * nc, n1 * nc * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, h->stream));
+        if (n1 < pending)
+            SW_CUDA(cudaMemcpyAsync(rows.data() + n1 * nc, h->d_ring, ((size_t)pending - n1) * nc *
+                                    sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
         SW_CUDA(cudaStreamSynchronize(h->stream));
-        std::vector<unsigned long long> rows((size_t)swgb::kRingSlots * h->ncounters);
-        SW_CUDA(cudaMemcpy(rows.data(), h->d_ring, rows.size() * sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost));
-        std::vector<int64_t> row(h->ncounters);
-        for (uint64_t t = h->t_drained; t < h->t_host; ++t) {
-            const size_t slot = (size_t)(t % swgb::kRingSlots);
-            for (int c = 0; c < h->ncounters; ++c) row[c] = (int64_t)rows[slot * h->ncounters + c];
+        std::vector<int64_t> row(nc);
+        for (size_t k = 0; k < (size_t)pending; ++k) {
+            for (size_t c = 0; c < nc; ++c) row[c] = (int64_t)rows[k * nc + c];
             accumulate(h, row.data());
         }
     }
@@ -543,10 +549,21 @@ int sw_set_spins(sw_handle *h, const int8_t *host, size_t n)
 {
     if (!h || !host) return fail(SW_ERR_ARG, "null argument");
     if (n != (size_t)h->L * h->L) return fail(SW_ERR_ARG, "n=%zu != L*L", n);
-    for (size_t i = 0; i < n; ++i)
-        if (host[i] < 0 || host[i] >= h->q) return fail(SW_ERR_ARG, "spin %zu = %d outside [0, q)", i, host[i]);
     SW_CUDA(cudaMemcpyAsync(h->d_spin, host, n, cudaMemcpyHostToDevice, h->stream));
+    // Range check on the device: the scratch word of the state block.
+    unsigned int *bad = &h->d_st->scratch;
+    SW_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), h->stream));
+    cudaError_t e = swgb::launch_count_invalid(h->lattice(), bad, h->sm_count, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_count_invalid");
+    unsigned int nbad = 0;
+    SW_CUDA(cudaMemcpyAsync(&nbad, bad, sizeof nbad, cudaMemcpyDeviceToHost, h->stream));
     SW_CUDA(cudaStreamSynchronize(h->stream));
+    if (nbad) {
+        // Leave a valid configuration behind: every kernel assumes states in [0, q).
+        SW_CUDA(cudaMemsetAsync(h->d_spin, 0, n, h->stream));
+        SW_CUDA(cudaStreamSynchronize(h->stream));
+        return fail(SW_ERR_ARG, "%u spins outside [0, %d); the lattice was reset to state 0", nbad, h->q);
+    }
     return SW_OK;
 }
 

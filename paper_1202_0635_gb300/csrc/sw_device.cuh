@@ -26,7 +26,7 @@ struct DevState {
     unsigned int ticket;               // blocks finished in the sweep's last kernel
     int err;                           // first device error (kErr*)
     int err_where;                     // site or index that hit it
-    int pad;
+    unsigned int scratch;              // host-side checks (count of invalid spins)
 };
 
 // Everything a kernel needs about one lattice.  Passed by value.

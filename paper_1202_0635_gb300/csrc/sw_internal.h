@@ -34,6 +34,8 @@ cudaError_t launch_init(const Lattice &lat, int random, int sm_count, cudaStream
 // Bond classes of the current configuration, if the last sweep's are still
 // missing (measurement on, before the host reads the counters).
 cudaError_t launch_pending_classes(const Lattice &lat, int sm_count, cudaStream_t s);
+// Number of spins outside [0, q) is added to *bad (device word).
+cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_count, cudaStream_t s);
 // ev (optional): events recorded before the first and after every kernel of
 // the sweep (kMaxStages + 1 entries).
 constexpr int kMaxStages = 4;

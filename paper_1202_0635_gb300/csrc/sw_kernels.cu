@@ -714,6 +714,16 @@ __global__ void k_mark_classes(DevState *st)
     st->classes_upto = st->sweep;
 }
 
+// Count states outside [0, q) (spins written by the caller).
+__global__ void k_count_invalid(const int8_t *spin, long long n, int q, unsigned int *bad)
+{
+    unsigned int c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        c += (spin[i] < 0 || spin[i] >= q);
+    c = __reduce_add_sync(FULL, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
+}
+
 template <bool CLOCK, bool MEASURE, bool LABELS>
 cudaError_t sweep_impl(const Lattice &lat, int sm_count, cudaStream_t s, cudaEvent_t *ev)
 {
@@ -769,6 +779,14 @@ cudaError_t launch_pending_classes(const Lattice &lat, int sm_count, cudaStream_
     else
         k_pending_classes<false><<<blocks, kEnergyThreads, 0, s>>>(lat);
     k_mark_classes<<<1, 1, 0, s>>>(lat.st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_count, cudaStream_t s)
+{
+    const long long n = (long long)lat.L * lat.L;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)sm_count * 4);
+    k_count_invalid<<<blocks, 256, 0, s>>>(lat.spin, n, lat.q, bad);
     return cudaGetLastError();
 }
 
