@@ -79,6 +79,7 @@ enum sw_init_mode { SW_INIT_UP = 0, SW_INIT_RANDOM = 1 };
 #define SW_MAX_COUNTERS (SW_MAX_Q + SW_MAX_Q / 2 + 1 + 2)
 
 typedef struct sw_handle sw_handle;
+typedef struct sw_batch sw_batch;
 
 /* Observables after the last sweep plus running means since sw_reset_stats
  * (Sec. 4: energy, magnetisation, moment ratio U = <M^4>/<M^2>^2, Eq. U).
@@ -186,6 +187,37 @@ int sw_set_graph(sw_handle *h, int on);
  *   3 cluster draws + spin write (+ state counts).
  * The sweeps count like any others.  Returns the number of stages (>0). */
 int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices (any mix of L, q, model, T, seed)
+ * advanced together, one launch sequence per sweep for all of them.  Every
+ * lattice's chain is identical to sweeping it alone (same kernels, same
+ * keys).  A batch references handles it does not own; attached handles run
+ * on the batch's stream and keep working with every per-handle getter
+ * (sw_measure, sw_get_spins, ...).
+ * ---------------------------------------------------------------------- */
+
+/* New empty batch on `stream` (a cudaStream_t; NULL: the batch makes one). */
+sw_batch *sw_batch_create(void *stream);
+/* Detach every lattice (they stay valid) and free the batch.  NULL-safe. */
+int sw_batch_destroy(sw_batch *b);
+/* Add / remove a lattice.  Attaching waits for the lattice's pending work
+ * and moves it to the batch's stream and measurement setting; a lattice
+ * can be in one batch at a time.  Detaching gives it a stream of its own.
+ * sw_destroy detaches a lattice first. */
+int sw_batch_attach(sw_batch *b, sw_handle *h);
+int sw_batch_detach(sw_batch *b, sw_handle *h);
+int sw_batch_size(sw_batch *b);
+/* Enqueue n sweeps of every attached lattice (asynchronous). */
+int sw_batch_sweep(sw_batch *b, int n);
+/* Wait for the batch's stream; report the first sticky device error. */
+int sw_batch_synchronize(sw_batch *b);
+/* Measurement on/off, CUDA-graph replay, debug labels: as the per-handle calls. */
+int sw_batch_set_measure(sw_batch *b, int on);
+int sw_batch_set_graph(sw_batch *b, int on);
+int sw_batch_set_debug_labels(sw_batch *b, int on);
+/* As sw_profile_sweeps, for the batched launch sequence. */
+int sw_batch_profile_sweeps(sw_batch *b, int n, float *ms, int max_stages);
 
 #ifdef __cplusplus
 }

@@ -79,6 +79,18 @@ EXPORTS = [
     ("sw_set_stream", ctypes.c_int, [_H, ctypes.c_void_p]),
     ("sw_set_graph", ctypes.c_int, [_H, ctypes.c_int]),
     ("sw_profile_sweeps", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    ("sw_batch_create", ctypes.c_void_p, [ctypes.c_void_p]),
+    ("sw_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("sw_batch_attach", ctypes.c_int, [ctypes.c_void_p, _H]),
+    ("sw_batch_detach", ctypes.c_int, [ctypes.c_void_p, _H]),
+    ("sw_batch_size", ctypes.c_int, [ctypes.c_void_p]),
+    ("sw_batch_sweep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sw_batch_synchronize", ctypes.c_int, [ctypes.c_void_p]),
+    ("sw_batch_set_measure", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sw_batch_set_graph", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sw_batch_set_debug_labels", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sw_batch_profile_sweeps", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                               ctypes.c_int]),
 ]
 
 
@@ -231,6 +243,55 @@ def sw_profile_sweeps(h, n):
     return [float(v) for v in out[:m]]
 
 
+def sw_batch_create(stream=None):
+    b = lib().sw_batch_create(stream)
+    if not b:
+        raise SwError(SW_ERR_CUDA, sw_last_error())
+    return b
+
+
+def sw_batch_destroy(b):
+    return _check(lib().sw_batch_destroy(b))
+
+
+def sw_batch_attach(b, h):
+    return _check(lib().sw_batch_attach(b, h))
+
+
+def sw_batch_detach(b, h):
+    return _check(lib().sw_batch_detach(b, h))
+
+
+def sw_batch_size(b):
+    return _check(lib().sw_batch_size(b))
+
+
+def sw_batch_sweep(b, n=1):
+    return _check(lib().sw_batch_sweep(b, int(n)))
+
+
+def sw_batch_synchronize(b):
+    return _check(lib().sw_batch_synchronize(b))
+
+
+def sw_batch_set_measure(b, on):
+    return _check(lib().sw_batch_set_measure(b, int(bool(on))))
+
+
+def sw_batch_set_graph(b, on):
+    return _check(lib().sw_batch_set_graph(b, int(bool(on))))
+
+
+def sw_batch_set_debug_labels(b, on):
+    return _check(lib().sw_batch_set_debug_labels(b, int(bool(on))))
+
+
+def sw_batch_profile_sweeps(b, n):
+    out = np.zeros(8, dtype=np.float32)
+    m = _check(lib().sw_batch_profile_sweeps(b, int(n), _p(out, ctypes.c_float), 8))
+    return [float(v) for v in out[:m]]
+
+
 class Lattice:
     """Owning convenience wrapper over one sw_handle (same calls, fewer arguments)."""
 
@@ -288,3 +349,40 @@ class Lattice:
     @sweep_index.setter
     def sweep_index(self, t):
         sw_set_sweep(self.h, t)
+
+
+class Batch:
+    """Owning convenience wrapper over one sw_batch: lattices added here are
+    attached and destroyed with the batch."""
+
+    def __init__(self, stream=None):
+        self.b = sw_batch_create(stream)
+        self.lattices = []
+
+    def add(self, L, q, model, T, seed, init=SW_INIT_UP):
+        lat = Lattice(L, q, model, T, seed, init=init)
+        sw_batch_attach(self.b, lat.h)
+        self.lattices.append(lat)
+        return lat
+
+    def remove(self, lat):
+        sw_batch_detach(self.b, lat.h)
+        self.lattices.remove(lat)
+        return lat
+
+    def sweep(self, n=1):
+        return sw_batch_sweep(self.b, n)
+
+    def close(self):
+        if getattr(self, "b", None):
+            sw_batch_destroy(self.b)
+            self.b = None
+        for lat in getattr(self, "lattices", []):
+            lat.close()
+        self.lattices = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

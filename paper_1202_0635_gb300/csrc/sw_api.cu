@@ -9,12 +9,14 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "sw_internal.h"
 
+using swgb::Batch;
 using swgb::DevState;
 using swgb::Lattice;
 
@@ -75,6 +77,12 @@ struct sw_handle {
     int tiles_x = 0, tiles_y = 0;
     DevState *d_st = nullptr;
     unsigned long long *d_ring = nullptr;
+    // Batch-of-one view used by sw_sweep: descriptor, task / merge prefixes, ticket.
+    Lattice *d_self = nullptr;
+    int *d_task_off = nullptr;
+    long long *d_merge_off = nullptr;
+    unsigned int *d_ticket = nullptr;
+    sw_batch *owner = nullptr;   // batch this lattice is attached to, if any
     uint32_t thr = 0;
     std::vector<uint32_t> thr_tab;
     int ncounters = 0, nclass = 0;
@@ -116,6 +124,57 @@ struct sw_handle {
         lat.ncounters = ncounters;
         lat.nclass = nclass;
         return lat;
+    }
+
+    int ntiles() const { return tiles_x * tiles_y; }
+    int ntasks() const { return (ntiles() + swgb::kTaskWarps - 1) / swgb::kTaskWarps; }
+    long long nmerge() const { return (long long)L * (tiles_x + tiles_y); }
+
+    Batch self_batch() const
+    {
+        Batch b{};
+        b.lat = d_self;
+        b.task_off = d_task_off;
+        b.merge_off = d_merge_off;
+        b.ticket = d_ticket;
+        b.nrep = 1;
+        b.ntasks = ntasks();
+        b.nmerge = nmerge();
+        return b;
+    }
+};
+
+// A set of lattices swept together with one launch sequence per sweep.  The
+// batch references handles it does not own (sw_batch_attach / _detach).
+struct sw_batch {
+    std::vector<sw_handle *> reps;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    bool measure = true, labels = false, use_graph = false;
+    // device descriptor arrays (capacity grows; contents rewritten on change)
+    int cap = 0;
+    Lattice *d_lat = nullptr;
+    int *d_task_off = nullptr;
+    long long *d_merge_off = nullptr;
+    unsigned int *d_ticket = nullptr;
+    int ntasks = 0;
+    long long nmerge = 0;
+    bool dirty = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+
+    Batch view() const
+    {
+        Batch b{};
+        b.lat = d_lat;
+        b.task_off = d_task_off;
+        b.merge_off = d_merge_off;
+        b.ticket = d_ticket;
+        b.nrep = (int)reps.size();
+        b.ntasks = ntasks;
+        b.nmerge = nmerge;
+        return b;
     }
 };
 
@@ -240,23 +299,31 @@ int reset_device_index(sw_handle *h, uint64_t t)
     return SW_OK;
 }
 
-int enqueue_one(sw_handle *h)
+// One sweep of batch view b on stream s, from a captured graph when asked.
+int enqueue_sweep(const Batch &b, bool measure, bool labels, int sm_count, cudaStream_t s, bool use_graph,
+                  cudaGraph_t *graph, cudaGraphExec_t *exec)
 {
-    if (h->use_graph) {
-        if (!h->graph_exec) {
-            SW_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t le = swgb::launch_sweep(h->lattice(), h->measure, h->labels, h->sm_count, h->stream);
-            cudaError_t ce = cudaStreamEndCapture(h->stream, &h->graph);
+    if (use_graph) {
+        if (!*exec) {
+            SW_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            cudaError_t le = swgb::launch_sweep(b, measure, labels, sm_count, s);
+            cudaError_t ce = cudaStreamEndCapture(s, graph);
             if (le != cudaSuccess) return cuda_fail(le, "launch_sweep (capture)");
             if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-            SW_CUDA(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+            SW_CUDA(cudaGraphInstantiate(exec, *graph, 0));
         }
-        SW_CUDA(cudaGraphLaunch(h->graph_exec, h->stream));
+        SW_CUDA(cudaGraphLaunch(*exec, s));
         return SW_OK;
     }
-    cudaError_t e = swgb::launch_sweep(h->lattice(), h->measure, h->labels, h->sm_count, h->stream);
+    cudaError_t e = swgb::launch_sweep(b, measure, labels, sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch_sweep");
     return SW_OK;
+}
+
+int enqueue_one(sw_handle *h)
+{
+    return enqueue_sweep(h->self_batch(), h->measure, h->labels, h->sm_count, h->stream, h->use_graph, &h->graph,
+                         &h->graph_exec);
 }
 
 void free_handle(sw_handle *h)
@@ -273,6 +340,10 @@ void free_handle(sw_handle *h)
     if (h->d_cross) cudaFree(h->d_cross);
     if (h->d_st) cudaFree(h->d_st);
     if (h->d_ring) cudaFree(h->d_ring);
+    if (h->d_self) cudaFree(h->d_self);
+    if (h->d_task_off) cudaFree(h->d_task_off);
+    if (h->d_merge_off) cudaFree(h->d_merge_off);
+    if (h->d_ticket) cudaFree(h->d_ticket);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -378,6 +449,23 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
                             cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(e, "cudaMemcpy(thresholds)");
     }
+    // Batch-of-one view.
+    {
+        const Lattice self = h->lattice();
+        const int task_off[2] = {0, h->ntasks()};
+        const long long merge_off[2] = {0, h->nmerge()};
+        if ((e = cudaMalloc(&h->d_self, sizeof(Lattice))) != cudaSuccess) return bail(e, "cudaMalloc(descriptor)");
+        if ((e = cudaMalloc(&h->d_task_off, sizeof task_off)) != cudaSuccess) return bail(e, "cudaMalloc(tasks)");
+        if ((e = cudaMalloc(&h->d_merge_off, sizeof merge_off)) != cudaSuccess) return bail(e, "cudaMalloc(merge)");
+        if ((e = cudaMalloc(&h->d_ticket, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMalloc(ticket)");
+        if ((e = cudaMemcpy(h->d_self, &self, sizeof self, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy(descriptor)");
+        if ((e = cudaMemcpy(h->d_task_off, task_off, sizeof task_off, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy(tasks)");
+        if ((e = cudaMemcpy(h->d_merge_off, merge_off, sizeof merge_off, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy(merge)");
+        if ((e = cudaMemset(h->d_ticket, 0, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMemset(ticket)");
+    }
     if (reset_device_index(h, 0) != SW_OK) {
         free_handle(h);
         return nullptr;
@@ -410,6 +498,7 @@ sw_handle *sw_create_ext(int L, int q, int model, double T, uint64_t seed, void 
 
 int sw_destroy(sw_handle *h)
 {
+    if (h && h->owner) sw_batch_detach(h->owner, h);
     free_handle(h);
     return SW_OK;
 }
@@ -488,6 +577,7 @@ int sw_measure(sw_handle *h, sw_obs *out)
 int sw_set_measure(sw_handle *h, int on)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (h->owner) return fail(SW_ERR_STATE, "lattice is attached to a batch; use sw_batch_set_measure");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
     if (h->measure != (on != 0)) drop_graph(h);
@@ -611,6 +701,7 @@ int sw_set_sweep(sw_handle *h, uint64_t t)
 int sw_set_stream(sw_handle *h, void *stream)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (h->owner) return fail(SW_ERR_STATE, "lattice is attached to a batch; it runs on the batch's stream");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -633,7 +724,7 @@ int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages)
     for (int s = 0; s < n && rc == SW_OK; ++s) {
         if (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) rc = drain(h);
         if (rc != SW_OK) break;
-        cudaError_t e = swgb::launch_sweep(h->lattice(), h->measure, h->labels, h->sm_count, h->stream, ev);
+        cudaError_t e = swgb::launch_sweep(h->self_batch(), h->measure, h->labels, h->sm_count, h->stream, ev);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "launch_sweep");
             break;
@@ -665,6 +756,267 @@ int sw_set_graph(sw_handle *h, int on)
     if (h->use_graph != (on != 0)) drop_graph(h);
     h->use_graph = on != 0;
     return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+static void drop_batch_graph(sw_batch *b)
+{
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+}
+
+static void free_batch_arrays(sw_batch *b)
+{
+    if (b->d_lat) cudaFree(b->d_lat);
+    if (b->d_task_off) cudaFree(b->d_task_off);
+    if (b->d_merge_off) cudaFree(b->d_merge_off);
+    b->d_lat = nullptr;
+    b->d_task_off = nullptr;
+    b->d_merge_off = nullptr;
+    b->cap = 0;
+}
+
+// Rewrite the device descriptor arrays from the attached lattices.
+static int rebuild_batch(sw_batch *b)
+{
+    const int n = (int)b->reps.size();
+    if (n > b->cap) {
+        drop_batch_graph(b);
+        free_batch_arrays(b);
+        const int cap = std::max(16, std::max(n, 2 * b->cap));
+        SW_CUDA(cudaMalloc(&b->d_lat, sizeof(Lattice) * cap));
+        SW_CUDA(cudaMalloc(&b->d_task_off, sizeof(int) * (cap + 1)));
+        SW_CUDA(cudaMalloc(&b->d_merge_off, sizeof(long long) * (cap + 1)));
+        b->cap = cap;
+    }
+    std::vector<Lattice> lat(n);
+    std::vector<int> task_off(n + 1, 0);
+    std::vector<long long> merge_off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        lat[i] = b->reps[i]->lattice();
+        task_off[i + 1] = task_off[i] + b->reps[i]->ntasks();
+        merge_off[i + 1] = merge_off[i] + b->reps[i]->nmerge();
+    }
+    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge) drop_batch_graph(b);
+    b->ntasks = task_off[n];
+    b->nmerge = merge_off[n];
+    if (n) {
+        SW_CUDA(cudaMemcpyAsync(b->d_lat, lat.data(), sizeof(Lattice) * n, cudaMemcpyHostToDevice, b->stream));
+        SW_CUDA(cudaMemcpyAsync(b->d_task_off, task_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
+                                b->stream));
+        SW_CUDA(cudaMemcpyAsync(b->d_merge_off, merge_off.data(), sizeof(long long) * (n + 1),
+                                cudaMemcpyHostToDevice, b->stream));
+        SW_CUDA(cudaStreamSynchronize(b->stream));
+    }
+    b->dirty = false;
+    return SW_OK;
+}
+
+sw_batch *sw_batch_create(void *stream)
+{
+    sw_batch *b = new (std::nothrow) sw_batch();
+    if (!b) {
+        fail(SW_ERR_OOM, "host allocation failed");
+        return nullptr;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        if (stream) {
+            b->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_ticket, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        cuda_fail(e, "sw_batch_create");
+        if (b->d_ticket) cudaFree(b->d_ticket);
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return nullptr;
+    }
+    return b;
+}
+
+int sw_batch_destroy(sw_batch *b)
+{
+    if (!b) return SW_OK;
+    while (!b->reps.empty()) sw_batch_detach(b, b->reps.back());
+    cudaStreamSynchronize(b->stream);
+    drop_batch_graph(b);
+    free_batch_arrays(b);
+    if (b->d_ticket) cudaFree(b->d_ticket);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return SW_OK;
+}
+
+int sw_batch_attach(sw_batch *b, sw_handle *h)
+{
+    if (!b || !h) return fail(SW_ERR_ARG, "null argument");
+    if (h->owner) return fail(SW_ERR_STATE, "lattice is already attached to a batch");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    if (h->measure != b->measure) {
+        drop_graph(h);
+        h->measure = b->measure;
+    }
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    h->own_stream = false;
+    h->stream = b->stream;
+    drop_graph(h);
+    h->owner = b;
+    b->reps.push_back(h);
+    b->dirty = true;
+    drop_batch_graph(b);
+    return SW_OK;
+}
+
+int sw_batch_detach(sw_batch *b, sw_handle *h)
+{
+    if (!b || !h) return fail(SW_ERR_ARG, "null argument");
+    auto it = std::find(b->reps.begin(), b->reps.end(), h);
+    if (it == b->reps.end()) return fail(SW_ERR_STATE, "lattice is not attached to this batch");
+    int rc = drain(h);
+    b->reps.erase(it);
+    h->owner = nullptr;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess) {
+        h->stream = s;
+        h->own_stream = true;
+    }
+    drop_graph(h);
+    b->dirty = true;
+    drop_batch_graph(b);
+    return rc;
+}
+
+int sw_batch_size(sw_batch *b)
+{
+    if (!b) return fail(SW_ERR_ARG, "null batch");
+    return (int)b->reps.size();
+}
+
+int sw_batch_sweep(sw_batch *b, int n)
+{
+    if (!b) return fail(SW_ERR_ARG, "null batch");
+    if (n < 0) return fail(SW_ERR_ARG, "n=%d < 0", n);
+    if (b->reps.empty() || n == 0) return SW_OK;
+    if (b->dirty) {
+        int rc = rebuild_batch(b);
+        if (rc != SW_OK) return rc;
+    }
+    for (int s = 0; s < n; ++s) {
+        for (sw_handle *h : b->reps) {
+            if (h->sticky != SW_OK) return fail(h->sticky, "%s", h->sticky_msg.c_str());
+            if (b->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) {
+                int rc = drain(h);
+                if (rc != SW_OK) return rc;
+            }
+        }
+        int rc = enqueue_sweep(b->view(), b->measure, b->labels, b->sm_count, b->stream, b->use_graph, &b->graph,
+                               &b->graph_exec);
+        if (rc != SW_OK) return rc;
+        for (sw_handle *h : b->reps) {
+            h->t_host++;
+            if (!b->measure) h->t_drained = h->t_host;
+        }
+    }
+    return SW_OK;
+}
+
+int sw_batch_synchronize(sw_batch *b)
+{
+    if (!b) return fail(SW_ERR_ARG, "null batch");
+    SW_CUDA(cudaStreamSynchronize(b->stream));
+    for (sw_handle *h : b->reps) {
+        int rc = check_device_error(h);
+        if (rc != SW_OK) return rc;
+    }
+    return SW_OK;
+}
+
+int sw_batch_set_measure(sw_batch *b, int on)
+{
+    if (!b) return fail(SW_ERR_ARG, "null batch");
+    for (sw_handle *h : b->reps) {
+        int rc = drain(h);
+        if (rc != SW_OK) return rc;
+        h->measure = on != 0;
+        drop_graph(h);
+    }
+    if (b->measure != (on != 0)) drop_batch_graph(b);
+    b->measure = on != 0;
+    return SW_OK;
+}
+
+int sw_batch_set_graph(sw_batch *b, int on)
+{
+    if (!b) return fail(SW_ERR_ARG, "null batch");
+    if (b->use_graph != (on != 0)) drop_batch_graph(b);
+    b->use_graph = on != 0;
+    return SW_OK;
+}
+
+int sw_batch_set_debug_labels(sw_batch *b, int on)
+{
+    if (!b) return fail(SW_ERR_ARG, "null batch");
+    if (b->labels != (on != 0)) drop_batch_graph(b);
+    b->labels = on != 0;
+    return SW_OK;
+}
+
+int sw_batch_profile_sweeps(sw_batch *b, int n, float *ms, int max_stages)
+{
+    if (!b || !ms) return fail(SW_ERR_ARG, "null argument");
+    if (n < 1 || max_stages < 1) return fail(SW_ERR_ARG, "n and max_stages must be positive");
+    if (b->reps.empty()) return fail(SW_ERR_STATE, "empty batch");
+    if (b->dirty) {
+        int rc = rebuild_batch(b);
+        if (rc != SW_OK) return rc;
+    }
+    const int nstages = swgb::kMaxStages;
+    cudaEvent_t ev[swgb::kMaxStages + 1];
+    for (int k = 0; k <= nstages; ++k) SW_CUDA(cudaEventCreate(&ev[k]));
+    std::vector<double> acc(nstages, 0.0);
+    int rc = SW_OK;
+    for (int s = 0; s < n && rc == SW_OK; ++s) {
+        for (sw_handle *h : b->reps)
+            if (rc == SW_OK && b->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) rc = drain(h);
+        if (rc != SW_OK) break;
+        cudaError_t e = swgb::launch_sweep(b->view(), b->measure, b->labels, b->sm_count, b->stream, ev);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "launch_sweep");
+            break;
+        }
+        for (sw_handle *h : b->reps) {
+            h->t_host++;
+            if (!b->measure) h->t_drained = h->t_host;
+        }
+        e = cudaEventSynchronize(ev[nstages]);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaEventSynchronize");
+            break;
+        }
+        for (int k = 0; k < nstages; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (int k = 0; k <= nstages; ++k) cudaEventDestroy(ev[k]);
+    if (rc != SW_OK) return rc;
+    const int m = std::min(nstages, max_stages);
+    for (int k = 0; k < m; ++k) ms[k] = (float)(acc[k] / n);
+    return m;
 }
 
 }  // extern "C"

@@ -51,6 +51,20 @@ struct Lattice {
     int nclass;
 };
 
+// A set of lattices swept together; a single lattice is a batch of one.
+// Tiles are grouped into block tasks of kTaskWarps tiles of one lattice, so
+// every block works on one lattice at a time.
+constexpr int kTaskWarps = 4;
+struct Batch {
+    const Lattice *lat;            // [nrep] descriptors (device memory)
+    const int *task_off;           // [nrep + 1] prefix sums of ceil(tiles / kTaskWarps)
+    const long long *merge_off;    // [nrep + 1] prefix sums of L * (tiles_x + tiles_y)
+    unsigned int *ticket;          // blocks finished in the sweep's last kernel
+    int nrep;
+    int ntasks;
+    long long nmerge;
+};
+
 // Philox-4x32-10 (Salmon et al., SC'11).  Each round takes two 32x32->64
 // products; their high halves are mixed with the other two words and the
 // round key, and the key advances by the two Weyl increments.

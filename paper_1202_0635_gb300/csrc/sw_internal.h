@@ -39,7 +39,7 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
 // ev (optional): events recorded before the first and after every kernel of
 // the sweep (kMaxStages + 1 entries).
 constexpr int kMaxStages = 4;
-cudaError_t launch_sweep(const Lattice &lat, bool measure, bool labels, int sm_count, cudaStream_t s,
+cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, cudaStream_t s,
                          cudaEvent_t *ev = nullptr);
 
 }  // namespace swgb

@@ -2,14 +2,14 @@
 //
 // One sweep (Komura & Okabe, arXiv:1202.0635, Sec. 2 steps (i)-(viii);
 // clock model: Sec. 4 embedded clusters) is four launches over 32 x 32
-// tiles.  A warp owns a tile; lane r owns row r of it as 32-bit masks.
+// tiles of every lattice of a batch (a single lattice is a batch of one).
+// A warp owns a tile; a block owns kTaskWarps tiles of one lattice at a
+// time ("task"), so per-lattice counters reduce per block.
 //
 //   k_label_tiles  bonds of every site (Sec. 2 (ii)): equal-neighbour masks
 //                  from packed byte compares, Philox draws against the
-//                  integer threshold.  Horizontal runs of right bonds come
-//                  from bit arithmetic; a union-find over run starts in
-//                  shared memory joins runs across the vertical bonds that
-//                  are not implied by a neighbouring column.  A component
+//                  integer threshold.  Tile-local clusters by a scanline over
+//                  the rows with a union-find in shared memory.  A component
 //                  that does not reach the tile border (or reaches it only
 //                  through inactive crossing bonds on the right/bottom
 //                  edges) is a finished cluster: its root (smallest site)
@@ -27,7 +27,7 @@
 //                  label") and counts those roots.
 //   k_flip_tiles   draws the new state of every open cluster root, writes
 //                  all spins, counts states; its last block advances the
-//                  sweep index.
+//                  sweep index of every lattice of the batch.
 #include "sw_internal.h"
 
 namespace swgb {
@@ -35,14 +35,14 @@ namespace swgb {
 namespace {
 
 constexpr int TW = kTileW, TH = kTileH, NS = kTileSites;
-constexpr int kWarpsLabel = 4;   // tiles in flight per k_label_tiles block
-constexpr int kWarpsFlip = 8;    // tiles in flight per k_flip_tiles block
-constexpr int kFlatWarps = 8;    // tiles per k_flatten block
+constexpr int kBlockThreads = kTaskWarps * 32;
 constexpr int kEnergyThreads = 256;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint16_t kCodeFlip = 0x4000;   // closed clock cluster: reflected
+constexpr int kNone = 0x7FFFFFFF;
 
 static_assert(TW == 32 && TH == 32, "the warp-tile layout assumes 32 x 32 tiles");
+static_assert(sizeof(Lattice) % 8 == 0, "lattice descriptors are copied in 8-byte words");
 
 __device__ __forceinline__ unsigned long long read_u64(const unsigned long long *p)
 {
@@ -56,10 +56,31 @@ __device__ __forceinline__ unsigned long long *ring_row(const Lattice &lat, unsi
 
 __device__ __forceinline__ int tid2d() { return threadIdx.y * blockDim.x + threadIdx.x; }
 
-// Global site index of tile-local index loc (row * 32 + column) in tile (bx, by).
-__device__ __forceinline__ int tile_site(const Lattice &lat, int bx, int by, int loc)
+// Largest r with off[r] <= k, for off[0] = 0 <= k < off[n].
+template <typename T>
+__device__ __forceinline__ int find_rep(const T *off, int n, T k)
 {
-    return (by * TH + (loc >> 5)) * lat.L + bx * TW + (loc & 31);
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= k) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Copy a lattice descriptor into shared memory (whole block).
+__device__ __forceinline__ void load_lattice(Lattice *dst, const Lattice *src)
+{
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(Lattice) / 8); i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// Global site index of tile-local index loc (row * 32 + column) in tile (bx, by).
+__device__ __forceinline__ int tile_site(int L, int bx, int by, int loc)
+{
+    return (by * TH + (loc >> 5)) * L + bx * TW + (loc & 31);
 }
 
 // Bit k of the result is set iff byte k of x is zero.
@@ -74,46 +95,6 @@ __device__ __forceinline__ unsigned zero_bytes4(unsigned x)
 __device__ __forceinline__ int start_of(unsigned S, int c)
 {
     return 31 - __clz(S & (FULL >> (31 - c)));
-}
-
-// Shared-memory slot of tile-local node x = row * 32 + column.  Lane r
-// works on row r, so storing column c at c ^ r puts the 32 lanes' accesses
-// to the same column in 32 different banks.
-__device__ __forceinline__ int sw_slot(int x)
-{
-    return x ^ ((x >> 5) & 31);
-}
-
-// Union-find over tile-local nodes stored at swizzled slots; same
-// invariants as the global one (parent <= node, roots are minima).
-__device__ __forceinline__ int find_t(volatile int *par, int x, int cap)
-{
-    for (int it = 0; it < cap; ++it) {
-        const int p = par[sw_slot(x)];
-        if (p == x) return x;
-        const int gp = par[sw_slot(p)];
-        if (gp == p) return p;
-        par[sw_slot(x)] = gp;
-        x = gp;
-    }
-    return -1;
-}
-
-__device__ __forceinline__ bool union_t(volatile int *par, int a, int b, int cap)
-{
-    for (int it = 0; it < cap; ++it) {
-        a = find_t(par, a, cap);
-        b = find_t(par, b, cap);
-        if (a < 0 || b < 0) return false;
-        if (a == b) return true;
-        const int hi = a > b ? a : b;
-        const int lo = a > b ? b : a;
-        const int old = atomicMin((int *)&par[sw_slot(hi)], lo);
-        if (old == hi) return true;
-        a = old;
-        b = lo;
-    }
-    return false;
 }
 
 __device__ __forceinline__ int byte_at(const uint32_t (&w)[8], int c)
@@ -153,6 +134,23 @@ __device__ __forceinline__ void add_hist_any(unsigned int *hist, int v, bool val
     }
 }
 
+// Per-lattice values every block needs once per task.
+struct TaskCtx {
+    unsigned long long t;   // sweep index
+    int count_classes;      // bond classes of configuration t - 1 are counted now
+    int m;                  // clock mirror axis
+};
+
+template <bool MEASURE>
+__device__ __forceinline__ TaskCtx task_context(const Lattice &lat)
+{
+    TaskCtx c;
+    c.t = read_u64(&lat.st->sweep);
+    c.count_classes = MEASURE && c.t >= 1ull && c.t - 1ull >= read_u64(&lat.st->classes_upto);
+    c.m = lat.clock ? clock_axis(lat, c.t) : 0;
+    return c;
+}
+
 // ---------------------------------------------------------------------------
 // k_init: all-up or random start (tag INIT, index = site, sweep field 0).
 // ---------------------------------------------------------------------------
@@ -174,29 +172,30 @@ __global__ void k_init(Lattice lat, int random)
 }
 
 // ---------------------------------------------------------------------------
-// k_label_tiles: one warp per 32 x 32 tile (grid-stride over tiles).
+// k_label_tiles
 //
 // Phase A (lane r = row r): bond masks of the row.  Phase B (lane c =
 // column c): a scanline over the rows.  Every site's parent word holds the
 // label of its run; a run of row y+1 takes the smallest root among the
-// runs of row y it touches (one redux over the run's lanes), and the other
-// touched roots are linked under it.  Roots therefore stay the smallest
-// site index of their component.  Phase C: resolve every site's root, mark
-// components that reach the tile border, draw the closed ones and write
-// the per-site codes.
+// runs of row y it touches (segmented shuffle min-scan over the run's
+// lanes), and the other touched roots are linked under it.  Roots thus stay
+// the smallest site index of their component.  Phase C: resolve every
+// site's root, mark components that reach the tile border, draw the closed
+// ones and write the per-site codes.
 // ---------------------------------------------------------------------------
-template <bool CLOCK, bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
+template <bool MEASURE, bool LABELS>
+__global__ void __launch_bounds__(kBlockThreads) k_label_tiles(Batch b)
 {
-    __shared__ int par_all[kWarpsLabel][NS];
-    __shared__ uint16_t rcode_all[kWarpsLabel][NS];
-    __shared__ uint16_t roots_all[kWarpsLabel][NS];
-    __shared__ unsigned int rowS_all[kWarpsLabel][32], rowR_all[kWarpsLabel][32], rowD_all[kWarpsLabel][32];
-    __shared__ unsigned int openw_all[kWarpsLabel][32];
-    __shared__ int nopen_all[kWarpsLabel];
+    __shared__ int par_all[kTaskWarps][NS];
+    __shared__ uint16_t rcode_all[kTaskWarps][NS];
+    __shared__ uint16_t roots_all[kTaskWarps][NS];
+    __shared__ unsigned int rowS_all[kTaskWarps][32], rowR_all[kTaskWarps][32], rowD_all[kTaskWarps][32];
+    __shared__ unsigned int openw_all[kTaskWarps][32];
+    __shared__ int nopen_all[kTaskWarps];
     __shared__ unsigned int hist_class[SW_MAX_CLOCK_Q / 2 + 2];
     __shared__ unsigned int red[32];
-    __shared__ int s_axis;
+    __shared__ __align__(16) Lattice lat;
+    __shared__ TaskCtx ctx;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *par = par_all[warp];
@@ -204,21 +203,51 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
     uint16_t *roots = roots_all[warp];
     unsigned int *rowS = rowS_all[warp], *rowR = rowR_all[warp], *rowD = rowD_all[warp];
     unsigned int *openw = openw_all[warp];
-    const int L = lat.L, q = lat.q;
-    const unsigned long long t = read_u64(&lat.st->sweep);
-    const bool count_classes = MEASURE && t >= 1ull && t - 1ull >= read_u64(&lat.st->classes_upto);
-    if (threadIdx.x == 0 && CLOCK) s_axis = clock_axis(lat, t);
-    if (MEASURE && CLOCK)
-        for (int k = threadIdx.x; k < lat.nclass; k += blockDim.x) hist_class[k] = 0u;
-    __syncthreads();
-    const int m = CLOCK ? s_axis : 0;
-    const uint32_t thr = lat.thr;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    constexpr int kNone = 0x7FFFFFFF;
 
     unsigned int active = 0, closed_roots = 0, unequal = 0, pairs = 0;
-    const int ntiles = lat.tiles_x * lat.tiles_y;
-    for (int tile = blockIdx.x * kWarpsLabel + warp; tile < ntiles; tile += gridDim.x * kWarpsLabel) {
+    int cur = -1;
+    // Counters of lattice `cur` -> its ring rows (whole block).
+    auto flush = [&]() {
+        if (MEASURE && cur >= 0) {
+            unsigned long long *row = ring_row(lat, ctx.t);
+            block_add<kBlockThreads>(row + lat.q + lat.nclass, active, red);
+            block_add<kBlockThreads>(row + lat.q + lat.nclass + 1, closed_roots, red);
+            if (ctx.count_classes) {
+                unsigned long long *prev = ring_row(lat, ctx.t - 1);
+                if (!lat.clock) {
+                    block_add<kBlockThreads>(prev + lat.q + 1, unequal, red);
+                    block_add<kBlockThreads>(prev + lat.q + 0, pairs - unequal, red);
+                } else {
+                    __syncthreads();
+                    for (int k = threadIdx.x; k < lat.nclass; k += blockDim.x)
+                        if (hist_class[k]) atomicAdd(prev + lat.q + k, (unsigned long long)hist_class[k]);
+                }
+            }
+        }
+        active = closed_roots = unequal = pairs = 0;
+        __syncthreads();
+    };
+
+    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
+        const int rep = find_rep(b.task_off, b.nrep, task);
+        if (rep != cur) {
+            flush();
+            load_lattice(&lat, b.lat + rep);
+            __syncthreads();
+            if (threadIdx.x == 0) ctx = task_context<MEASURE>(lat);
+            if (MEASURE)
+                for (int k = threadIdx.x; k < SW_MAX_CLOCK_Q / 2 + 2; k += blockDim.x) hist_class[k] = 0u;
+            __syncthreads();
+            cur = rep;
+        }
+        const int tile = (task - __ldg(b.task_off + rep)) * kTaskWarps + warp;
+        if (tile >= lat.tiles_x * lat.tiles_y) continue;   // whole warp
+        const int L = lat.L, q = lat.q;
+        const bool clock = lat.clock != 0;
+        const unsigned long long t = ctx.t;
+        const int m = ctx.m;
+        const uint32_t thr = lat.thr;
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int x0 = bx * TW, y0 = by * TH;
         const int ncols = min(TW, L - x0), nrows = min(TH, L - y0);
@@ -249,7 +278,7 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
                 for (int k = 0; k < 8; ++k) dn[k] = (4 * k < ncols) ? __ldg(drow + k) : 0u;
             }
             unsigned eqR = 0, eqD = 0, rR = 0, rD = 0;
-            if (!CLOCK) {
+            if (!clock) {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
@@ -259,32 +288,38 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
             }
             if (rv) {
                 const uint32_t pbase = (uint32_t)(rowbase >> 1);
+                if (!clock) {
 #pragma unroll
-                for (int p = 0; p < 16; ++p) {
-                    if (2 * p < ncols) {
-                        const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
-                        uint32_t tr0 = thr, tr1 = thr, td0 = thr, td1 = thr;
-                        if (CLOCK) {
+                    for (int p = 0; p < 16; ++p) {
+                        if (2 * p < ncols) {
+                            const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
+                            rR |= ((unsigned)(u.x < thr) << (2 * p)) | ((unsigned)(u.z < thr) << (2 * p + 1));
+                            rD |= ((unsigned)(u.y < thr) << (2 * p)) | ((unsigned)(u.w < thr) << (2 * p + 1));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 16; ++p) {
+                        if (2 * p < ncols) {
+                            const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
                             const int c0 = 2 * p, c1 = 2 * p + 1;
                             const int s0 = byte_at(wd, c0), s1 = byte_at(wd, c1);
                             const int s2 = (c1 + 1 < ncols) ? byte_at(wd, (c1 + 1) & 31) : (int)sr;
-                            tr0 = clock_thr(lat, s0, s1, m);
-                            tr1 = clock_thr(lat, s1, s2, m);
-                            td0 = clock_thr(lat, s0, byte_at(dn, c0), m);
-                            td1 = clock_thr(lat, s1, byte_at(dn, c1), m);
+                            rR |= ((unsigned)(u.x < clock_thr(lat, s0, s1, m)) << c0) |
+                                  ((unsigned)(u.z < clock_thr(lat, s1, s2, m)) << c1);
+                            rD |= ((unsigned)(u.y < clock_thr(lat, s0, byte_at(dn, c0), m)) << c0) |
+                                  ((unsigned)(u.w < clock_thr(lat, s1, byte_at(dn, c1), m)) << c1);
                         }
-                        rR |= ((unsigned)(u.x < tr0) << (2 * p)) | ((unsigned)(u.z < tr1) << (2 * p + 1));
-                        rD |= ((unsigned)(u.y < td0) << (2 * p)) | ((unsigned)(u.w < td1) << (2 * p + 1));
                     }
                 }
             }
-            const unsigned R = CLOCK ? (rR & V) : (rR & eqR & V);
-            const unsigned D = CLOCK ? (rD & V) : (rD & eqD & V);
+            const unsigned R = clock ? (rR & V) : (rR & eqR & V);
+            const unsigned D = clock ? (rD & V) : (rD & eqD & V);
 
             if (MEASURE) {
                 if (rv) active += __popc(R) + __popc(D);
-                if (count_classes) {
-                    if (!CLOCK) {
+                if (ctx.count_classes) {
+                    if (!clock) {
                         if (rv) {
                             unequal += __popc(~eqR & V) + __popc(~eqD & V);
                             pairs += 2u * (unsigned)ncols;
@@ -316,10 +351,7 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
         const int c = lane;
         const bool cv = c < ncols;
         const unsigned above_c = ~(FULL >> (31 - c));   // columns > c
-        {
-            const unsigned S0 = rowS[0];
-            par[c] = cv ? start_of(S0, c) : c;
-        }
+        par[c] = cv ? start_of(rowS[0], c) : c;
         for (int row = 0; row + 1 < nrows; ++row) {
             const unsigned Sn = rowS[row + 1], D = rowD[row], R = rowR[row], Rn = rowR[row + 1];
             // A vertical bond is implied by its left neighbour column when both
@@ -371,14 +403,14 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
                 if (open) atomicOr(&openw[root >> 5], 1u << (root & 31));
             }
             const bool isroot = cv && root == x;
-            const unsigned b = __ballot_sync(FULL, isroot);
-            if (isroot) roots[nroots + __popc(b & lanemask_lt)] = (uint16_t)x;
-            nroots += __popc(b);
+            const unsigned bal = __ballot_sync(FULL, isroot);
+            if (isroot) roots[nroots + __popc(bal & lanemask_lt)] = (uint16_t)x;
+            nroots += __popc(bal);
         }
         __syncwarp();
         for (int j = c; j < nroots; j += 32) {
             const int x = roots[j];
-            const int g = tile_site(lat, bx, by, x);
+            const int g = tile_site(L, bx, by, x);
             if ((openw[x >> 5] >> (x & 31)) & 1u) {
                 const int slot = atomicAdd(&nopen_all[warp], 1);
                 lat.open_list[(size_t)tile * kOpenSlots + slot] = g;
@@ -386,7 +418,7 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
                 rcode[x] = (uint16_t)x;
             } else {
                 const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
-                rcode[x] = CLOCK ? (uint16_t)(kCodeClosed | ((u >> 31) ? kCodeFlip : 0))
+                rcode[x] = clock ? (uint16_t)(kCodeClosed | ((u >> 31) ? kCodeFlip : 0))
                                  : (uint16_t)(kCodeClosed | mulhi_q(u, q));
                 ++closed_roots;
             }
@@ -397,11 +429,11 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
                 const size_t site = (size_t)(y0 + row) * L + x0 + c;
                 const int root = par[row * TW + c];
                 uint32_t code = rcode[root];
-                if (CLOCK && (code & kCodeClosed)) {
+                if (clock && (code & kCodeClosed)) {
                     const int k0 = valid_state(__ldg(lat.spin + site), q);
                     code = kCodeClosed | (uint32_t)((code & kCodeFlip) ? reflect(k0, m, q) : k0);
                 }
-                if (LABELS && (code & kCodeClosed)) lat.label[site] = tile_site(lat, bx, by, root);
+                if (LABELS && (code & kCodeClosed)) lat.label[site] = tile_site(L, bx, by, root);
                 lat.code[site] = (uint16_t)code;
             }
         }
@@ -412,28 +444,13 @@ __global__ void __launch_bounds__(kWarpsLabel * 32) k_label_tiles(Lattice lat)
         }
         __syncwarp();
     }
-
-    if (MEASURE) {
-        unsigned long long *row = ring_row(lat, t);
-        block_add<kWarpsLabel * 32>(row + q + lat.nclass, active, red);
-        block_add<kWarpsLabel * 32>(row + q + lat.nclass + 1, closed_roots, red);
-        if (count_classes) {
-            unsigned long long *prev = ring_row(lat, t - 1);
-            if (!CLOCK) {
-                block_add<kWarpsLabel * 32>(prev + q + 1, unequal, red);
-                block_add<kWarpsLabel * 32>(prev + q + 0, pairs - unequal, red);
-            } else {
-                __syncthreads();
-                for (int k = threadIdx.x; k < lat.nclass; k += blockDim.x)
-                    if (hist_class[k]) atomicAdd(prev + q + k, (unsigned long long)hist_class[k]);
-            }
-        }
-    }
+    flush();
 }
 
 // ---------------------------------------------------------------------------
 // k_merge: union of the open roots across every active crossing bond.
-// Work items: L * tiles_x right-edge bonds, then L * tiles_y bottom-edge bonds.
+// Work items of a lattice: L * tiles_x right-edge bonds, then L * tiles_y
+// bottom-edge bonds.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int open_root_of(const Lattice &lat, int site, bool &ok)
 {
@@ -443,27 +460,34 @@ __device__ __forceinline__ int open_root_of(const Lattice &lat, int site, bool &
         ok = false;
         return site;
     }
-    return tile_site(lat, sx / TW, sy / TH, code);
+    return tile_site(lat.L, sx / TW, sy / TH, code);
 }
 
-__global__ void k_merge(Lattice lat)
+__global__ void k_merge(Batch b)
 {
-    const int L = lat.L, ncol = lat.tiles_x;
-    const long long nright = (long long)L * ncol;
-    const long long total = nright + (long long)L * lat.tiles_y;
-    const int cap = L * L + 1;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+    long long lo = 0, hi = 0;
+    Lattice lat;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < b.nmerge;
          k += (long long)gridDim.x * blockDim.x) {
+        if (k < lo || k >= hi) {
+            const int rep = find_rep(b.merge_off, b.nrep, k);
+            lo = __ldg(b.merge_off + rep);
+            hi = __ldg(b.merge_off + rep + 1);
+            lat = b.lat[rep];
+        }
+        const int L = lat.L, ncol = lat.tiles_x;
+        const long long kk = k - lo;
+        const long long nright = (long long)L * ncol;
         int i, j;
-        if (k < nright) {
-            const int y = (int)(k / ncol), c = (int)(k % ncol);
+        if (kk < nright) {
+            const int y = (int)(kk / ncol), c = (int)(kk % ncol);
             const int tile = (y / TH) * ncol + c;
             if (!((__ldg(lat.cross + (size_t)tile * kCrossWords) >> (y % TH)) & 1u)) continue;
             const int x = min((c + 1) * TW, L) - 1;
             i = y * L + x;
             j = y * L + (x + 1 == L ? 0 : x + 1);
         } else {
-            const long long k2 = k - nright;
+            const long long k2 = kk - nright;
             const int rr = (int)(k2 / L), x = (int)(k2 % L);
             const int tile = rr * ncol + x / TW;
             if (!((__ldg(lat.cross + (size_t)tile * kCrossWords + 1) >> (x % TW)) & 1u)) continue;
@@ -472,12 +496,12 @@ __global__ void k_merge(Lattice lat)
             j = (y + 1 == L ? 0 : y + 1) * L + x;
         }
         bool ok = true;
-        const int a = open_root_of(lat, i, ok), b = open_root_of(lat, j, ok);
+        const int a = open_root_of(lat, i, ok), c2 = open_root_of(lat, j, ok);
         if (!ok) {   // a crossing bond always ends at open sites
             record_error(lat.st, kErrInternal, i);
             continue;
         }
-        union_roots(lat.label, a, b, cap, lat.st);
+        union_roots(lat.label, a, c2, L * L + 1, lat.st);
     }
 }
 
@@ -486,15 +510,32 @@ __global__ void k_merge(Lattice lat)
 // One warp per tile.
 // ---------------------------------------------------------------------------
 template <bool MEASURE>
-__global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(Lattice lat)
+__global__ void __launch_bounds__(kBlockThreads) k_flatten(Batch b)
 {
     __shared__ unsigned int red[32];
+    __shared__ __align__(16) Lattice lat;
+    __shared__ unsigned long long s_t;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * kFlatWarps + warp;
-    const int ntiles = lat.tiles_x * lat.tiles_y;
-    const int cap = lat.L * lat.L + 1;
     unsigned int roots = 0;
-    if (tile < ntiles) {
+    int cur = -1;
+    auto flush = [&]() {
+        if (MEASURE && cur >= 0) block_add<kBlockThreads>(ring_row(lat, s_t) + lat.q + lat.nclass + 1, roots, red);
+        roots = 0;
+        __syncthreads();
+    };
+    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
+        const int rep = find_rep(b.task_off, b.nrep, task);
+        if (rep != cur) {
+            flush();
+            load_lattice(&lat, b.lat + rep);
+            __syncthreads();
+            if (threadIdx.x == 0) s_t = read_u64(&lat.st->sweep);
+            __syncthreads();
+            cur = rep;
+        }
+        const int tile = (task - __ldg(b.task_off + rep)) * kTaskWarps + warp;
+        if (tile >= lat.tiles_x * lat.tiles_y) continue;
+        const int cap = lat.L * lat.L + 1;
         const int n = lat.open_count[tile];
         for (int s = lane; s < n; s += 32) {
             const int r = lat.open_list[(size_t)tile * kOpenSlots + s];
@@ -503,70 +544,93 @@ __global__ void __launch_bounds__(32 * kFlatWarps) k_flatten(Lattice lat)
             else ++roots;
         }
     }
-    if (MEASURE) {
-        const unsigned long long t = read_u64(&lat.st->sweep);
-        block_add<32 * kFlatWarps>(ring_row(lat, t) + lat.q + lat.nclass + 1, roots, red);
-    }
+    flush();
 }
 
-// Last block of the sweep's final kernel: record that the incoming
-// configuration's classes were counted, zero the next counter row and
-// advance the sweep index (every block has read it by then).
-__device__ void finish_sweep(const Lattice &lat, unsigned long long t, bool counted_classes)
+// Last block of the sweep's final kernel: for every lattice of the batch,
+// record that the incoming configuration's classes were counted, zero the
+// next counter row and advance the sweep index (every block has read it).
+template <bool MEASURE>
+__device__ void finish_sweep(const Batch &b)
 {
     __shared__ int s_last;
     __syncthreads();
-    const int tid = tid2d();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned int nblk = gridDim.x * gridDim.y;
-        const unsigned int prev = atomicAdd(&lat.st->ticket, 1u);
-        s_last = (prev == nblk - 1);
+        const unsigned int prev = atomicAdd(b.ticket, 1u);
+        s_last = (prev == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_last) {
+    if (!s_last) return;
+    __threadfence();
+    for (int r = threadIdx.x; r < b.nrep; r += blockDim.x) {
+        const Lattice &lt = b.lat[r];
+        const unsigned long long t = read_u64(&lt.st->sweep);
+        const bool counted = MEASURE && t >= 1ull && t - 1ull >= read_u64(&lt.st->classes_upto);
+        unsigned long long *next = ring_row(lt, t + 1);
+        for (int c = 0; c < lt.ncounters; ++c) next[c] = 0ull;
+        if (counted) lt.st->classes_upto = t;
         __threadfence();
-        unsigned long long *next = ring_row(lat, t + 1);
-        for (int c = tid; c < lat.ncounters; c += blockDim.x * blockDim.y) next[c] = 0ull;
-        if (tid == 0) {
-            lat.st->ticket = 0u;
-            if (counted_classes) lat.st->classes_upto = t;
-            *reinterpret_cast<volatile unsigned long long *>(&lat.st->sweep) = t + 1;
-        }
+        *reinterpret_cast<volatile unsigned long long *>(&lt.st->sweep) = t + 1;
     }
+    if (threadIdx.x == 0) *b.ticket = 0u;
 }
 
 // ---------------------------------------------------------------------------
 // k_flip_tiles: new states of open clusters, all spin writes, state counts.
-// One warp per tile (grid-stride); lane r writes row r.
+// One warp per tile; lane r writes row r.
 // ---------------------------------------------------------------------------
-template <bool CLOCK, bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kWarpsFlip * 32) k_flip_tiles(Lattice lat)
+template <bool MEASURE, bool LABELS>
+__global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
 {
-    __shared__ unsigned char tab_all[kWarpsFlip][NS];
-    __shared__ int rootg_all[LABELS ? kWarpsFlip : 1][LABELS ? NS : 1];
+    __shared__ unsigned char tab_all[kTaskWarps][NS];
+    __shared__ int rootg_all[LABELS ? kTaskWarps : 1][LABELS ? NS : 1];
     __shared__ unsigned int hist_state[SW_MAX_Q + 1];
-    __shared__ int s_axis;
+    __shared__ __align__(16) Lattice lat;
+    __shared__ TaskCtx ctx;
 
     const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
     unsigned char *tab = tab_all[warp];
-    const int L = lat.L, q = lat.q;
-    const unsigned long long t = read_u64(&lat.st->sweep);
-    const bool counted_classes = MEASURE && t >= 1ull && t - 1ull >= read_u64(&lat.st->classes_upto);
-    const int cap = L * L + 1;
-    if (threadIdx.x == 0 && CLOCK) s_axis = clock_axis(lat, t);
-    if (MEASURE)
-        for (int k = threadIdx.x; k < q; k += blockDim.x) hist_state[k] = 0u;
-    __syncthreads();
-    const int m = CLOCK ? s_axis : 0;
-
     // q <= 8: state counts of this lane, 16 bits per state (states 0-3, 4-7).
     unsigned long long cnt_lo = 0, cnt_hi = 0;
-    const int ntiles = lat.tiles_x * lat.tiles_y;
-    for (int tile = blockIdx.x * kWarpsFlip + warp; tile < ntiles; tile += gridDim.x * kWarpsFlip) {
-        const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
+    int cur = -1;
+    auto flush = [&]() {
+        if (MEASURE && cur >= 0) {
+            if (lat.q <= 8) {
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const unsigned long long w = s < 4 ? cnt_lo : cnt_hi;
+                    const unsigned int v = __reduce_add_sync(FULL, (unsigned int)((w >> (16 * (s & 3))) & 0xFFFFull));
+                    if (r == 0 && s < lat.q && v) atomicAdd(&hist_state[s], v);
+                }
+            }
+            __syncthreads();
+            unsigned long long *row = ring_row(lat, ctx.t);
+            for (int k = threadIdx.x; k < lat.q; k += blockDim.x)
+                if (hist_state[k]) atomicAdd(row + k, (unsigned long long)hist_state[k]);
+        }
+        cnt_lo = cnt_hi = 0;
+        __syncthreads();
+    };
+    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
+        const int rep = find_rep(b.task_off, b.nrep, task);
+        if (rep != cur) {
+            flush();
+            load_lattice(&lat, b.lat + rep);
+            __syncthreads();
+            if (threadIdx.x == 0) ctx = task_context<MEASURE>(lat);
+            for (int k = threadIdx.x; k < SW_MAX_Q + 1; k += blockDim.x) hist_state[k] = 0u;
+            __syncthreads();
+            cur = rep;
+        }
+        const int tile = (task - __ldg(b.task_off + rep)) * kTaskWarps + warp;
+        const bool have = tile < lat.tiles_x * lat.tiles_y;
+        const int L = lat.L, q = lat.q;
+        const bool clock = lat.clock != 0;
+        const int m = ctx.m;
+        const int by = have ? tile / lat.tiles_x : 0, bx = have ? tile - by * lat.tiles_x : 0;
         const int x0 = bx * TW, y0 = by * TH;
-        const int ncols = min(TW, L - x0), nrows = min(TH, L - y0);
+        const int ncols = have ? min(TW, L - x0) : 0, nrows = have ? min(TH, L - y0) : 0;
         const bool rv = r < nrows;
         const size_t rowbase = (size_t)(y0 + r) * L + x0;
 
@@ -578,16 +642,16 @@ __global__ void __launch_bounds__(kWarpsFlip * 32) k_flip_tiles(Lattice lat)
         for (int k = 0; k < 8; ++k) {
             const bool v = rv && 4 * k < ncols;
             cw[k] = v ? reinterpret_cast<const uint2 *>(lat.code + rowbase)[k] : make_uint2(0u, 0u);
-            sw[k] = (CLOCK && v) ? reinterpret_cast<const uint32_t *>(lat.spin + rowbase)[k] : 0u;
+            sw[k] = (clock && v) ? reinterpret_cast<const uint32_t *>(lat.spin + rowbase)[k] : 0u;
         }
-        const int n = lat.open_count[tile];
+        const int n = have ? lat.open_count[tile] : 0;
         for (int s = r; s < n; s += 32) {
             const int rg = lat.open_list[(size_t)tile * kOpenSlots + s];
-            const int g = find_root_ro(lat.label, rg, cap, lat.st);
-            const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
+            const int g = find_root_ro(lat.label, rg, L * L + 1, lat.st);
+            const uint32_t u = draw4(lat, (uint32_t)g, ctx.t, kTagState).x;
             const int ry = rg / L, rx = rg - ry * L;
             const int loc = (ry - y0) * TW + (rx - x0);
-            tab[loc] = CLOCK ? (unsigned char)(u >> 31) : (unsigned char)mulhi_q(u, q);
+            tab[loc] = clock ? (unsigned char)(u >> 31) : (unsigned char)mulhi_q(u, q);
             if (LABELS) rootg_all[LABELS ? warp : 0][LABELS ? loc : 0] = g;
         }
         __syncwarp();
@@ -603,7 +667,7 @@ __global__ void __launch_bounds__(kWarpsFlip * 32) k_flip_tiles(Lattice lat)
                     int ns;
                     if (code & kCodeClosed) {
                         ns = (int)(code & 0x7Fu);
-                    } else if (CLOCK) {
+                    } else if (clock) {
                         const int k0 = valid_state((int)((sw[k] >> (8 * h)) & 0xFFu), q);
                         ns = tab[code] ? reflect(k0, m, q) : k0;
                     } else {
@@ -634,21 +698,8 @@ __global__ void __launch_bounds__(kWarpsFlip * 32) k_flip_tiles(Lattice lat)
         }
         __syncwarp();
     }
-    if (MEASURE) {
-        if (q <= 8) {
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const unsigned long long w = s < 4 ? cnt_lo : cnt_hi;
-                const unsigned int v = __reduce_add_sync(FULL, (unsigned int)((w >> (16 * (s & 3))) & 0xFFFFull));
-                if (r == 0 && s < q && v) atomicAdd(&hist_state[s], v);
-            }
-        }
-        __syncthreads();
-        unsigned long long *row = ring_row(lat, t);
-        for (int k = threadIdx.x; k < q; k += blockDim.x)
-            if (hist_state[k]) atomicAdd(row + k, (unsigned long long)hist_state[k]);
-    }
-    finish_sweep(lat, t, counted_classes);
+    flush();
+    finish_sweep<MEASURE>(b);
 }
 
 // ---------------------------------------------------------------------------
@@ -673,7 +724,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_pending_classes(Lattice lat)
     for (long long base = (long long)blockIdx.x * blockDim.x; base < N4; base += (long long)gridDim.x * blockDim.x) {
         const long long g = base + threadIdx.x;
         const bool v = g < N4;
-        int a[8] = {0, 0, 0, 0, 0, 0, 0, 0}, b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int a[8] = {0, 0, 0, 0, 0, 0, 0, 0}, bb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (v) {
             const int i0 = (int)(4 * g);
             const int y = i0 / L, x = i0 - y * L;
@@ -682,20 +733,20 @@ __global__ void __launch_bounds__(kEnergyThreads) k_pending_classes(Lattice lat)
             const char4 d = *reinterpret_cast<const char4 *>(lat.spin + (size_t)yd * L + x);
             const int sr = lat.spin[(size_t)y * L + ((x + 4 == L) ? 0 : x + 4)];
             const int aa[8] = {s.x, s.y, s.z, s.w, s.x, s.y, s.z, s.w};
-            const int bb[8] = {s.y, s.z, s.w, sr, d.x, d.y, d.z, d.w};
+            const int b2[8] = {s.y, s.z, s.w, sr, d.x, d.y, d.z, d.w};
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 a[k] = aa[k];
-                b[k] = bb[k];
+                bb[k] = b2[k];
             }
             sites += 4;
         }
         if (CLOCK) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) add_hist_any(hist, clock_bond_class(a[k], b[k], q), v);
+            for (int k = 0; k < 8; ++k) add_hist_any(hist, clock_bond_class(a[k], bb[k], q), v);
         } else if (v) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) unequal += (a[k] != b[k]);
+            for (int k = 0; k < 8; ++k) unequal += (a[k] != bb[k]);
         }
     }
     unsigned long long *row = ring_row(lat, t - 1);
@@ -724,39 +775,27 @@ __global__ void k_count_invalid(const int8_t *spin, long long n, int q, unsigned
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
 }
 
-template <bool CLOCK, bool MEASURE, bool LABELS>
-cudaError_t sweep_impl(const Lattice &lat, int sm_count, cudaStream_t s, cudaEvent_t *ev)
+template <bool MEASURE, bool LABELS>
+cudaError_t sweep_impl(const Batch &b, int sm_count, cudaStream_t s, cudaEvent_t *ev)
 {
     int nev = 0;
     auto mark = [&]() {
         if (ev) cudaEventRecord(ev[nev++], s);
     };
-    const int ntiles = lat.tiles_x * lat.tiles_y;
+    const int blocks = std::max(1, std::min(b.ntasks, sm_count * 8));
     mark();
-    const int lblocks = std::min((ntiles + kWarpsLabel - 1) / kWarpsLabel, sm_count * 8);
-    k_label_tiles<CLOCK, MEASURE, LABELS><<<lblocks, kWarpsLabel * 32, 0, s>>>(lat);
+    k_label_tiles<MEASURE, LABELS><<<blocks, kBlockThreads, 0, s>>>(b);
     mark();
-    const long long nmerge = (long long)lat.L * (lat.tiles_x + lat.tiles_y);
-    const int mblocks = (int)std::min<long long>((nmerge + 255) / 256, (long long)sm_count * 16);
-    k_merge<<<mblocks, 256, 0, s>>>(lat);
+    const int mblocks =
+        (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * 16));
+    k_merge<<<mblocks, 256, 0, s>>>(b);
     mark();
-    k_flatten<MEASURE><<<(ntiles + kFlatWarps - 1) / kFlatWarps, 32 * kFlatWarps, 0, s>>>(lat);
+    const int fblocks = std::max(1, std::min(b.ntasks, sm_count * 16));
+    k_flatten<MEASURE><<<fblocks, kBlockThreads, 0, s>>>(b);
     mark();
-    const int fblocks = std::min((ntiles + kWarpsFlip - 1) / kWarpsFlip, sm_count * 8);
-    k_flip_tiles<CLOCK, MEASURE, LABELS><<<fblocks, kWarpsFlip * 32, 0, s>>>(lat);
+    k_flip_tiles<MEASURE, LABELS><<<fblocks, kBlockThreads, 0, s>>>(b);
     mark();
     return cudaGetLastError();
-}
-
-template <bool CLOCK>
-cudaError_t sweep_dispatch(const Lattice &lat, bool measure, bool labels, int sm_count, cudaStream_t s,
-                           cudaEvent_t *ev)
-{
-    if (measure)
-        return labels ? sweep_impl<CLOCK, true, true>(lat, sm_count, s, ev)
-                      : sweep_impl<CLOCK, true, false>(lat, sm_count, s, ev);
-    return labels ? sweep_impl<CLOCK, false, true>(lat, sm_count, s, ev)
-                  : sweep_impl<CLOCK, false, false>(lat, sm_count, s, ev);
 }
 
 }  // namespace
@@ -790,11 +829,12 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const Lattice &lat, bool measure, bool labels, int sm_count, cudaStream_t s,
+cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, cudaStream_t s,
                          cudaEvent_t *ev)
 {
-    if (lat.clock) return sweep_dispatch<true>(lat, measure, labels, sm_count, s, ev);
-    return sweep_dispatch<false>(lat, measure, labels, sm_count, s, ev);
+    if (measure)
+        return labels ? sweep_impl<true, true>(b, sm_count, s, ev) : sweep_impl<true, false>(b, sm_count, s, ev);
+    return labels ? sweep_impl<false, true>(b, sm_count, s, ev) : sweep_impl<false, false>(b, sm_count, s, ev);
 }
 
 }  // namespace swgb

@@ -1,0 +1,106 @@
+"""Batched sweeps through the C ABI (needs a GB300): every lattice of a
+batch of mixed sizes, models and temperatures follows exactly the chain it
+follows alone, and the oracle's."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1202_0635_gb300 as sw
+from oracle import CLOCK, ISING, POTTS, Oracle
+
+pytestmark = pytest.mark.gpu
+
+MODEL = {POTTS: sw.SW_POTTS, CLOCK: sw.SW_CLOCK, ISING: sw.SW_ISING}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1202_0635_gb300 import build
+    build.build()
+    sw.lib()
+
+
+def mixed_replicas(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n):
+        kind = rng.integers(0, 3)
+        L = int(rng.choice([8, 32, 36, 64, 100, 128, 264]))
+        if kind == 0:
+            q, model, Tc = 2, POTTS, 1.0 / math.log(1.0 + math.sqrt(2.0))
+        elif kind == 1:
+            q, model, Tc = 3, POTTS, 1.0 / math.log(1.0 + math.sqrt(3.0))
+        else:
+            q, model, Tc = 6, CLOCK, 0.9
+        out.append((L, q, model, Tc * rng.uniform(0.8, 1.2), 1000 + r))
+    return out
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_plain_and_oracle(graph):
+    reps = mixed_replicas(12, 3)
+    b = sw.Batch()
+    sw.sw_batch_set_graph(b.b, graph)
+    lats = [b.add(L, q, MODEL[m], T, s, init=sw.SW_INIT_RANDOM) for (L, q, m, T, s) in reps]
+    for lat in lats:
+        sw.sw_set_record(lat.h, 1)
+    refs = [Oracle(L, q, m, T, s, init="random") for (L, q, m, T, s) in reps]
+    for step in range(6):
+        b.sweep(3)
+        for (L, q, m, T, s), lat, ref in zip(reps, lats, refs):
+            rec = ref.sweep(3, record=True)
+            assert np.array_equal(lat.spins, ref.spins), (L, q, m, step)
+            assert np.array_equal(lat.take_counts(), rec), (L, q, m, step)
+    alone = []
+    for (L, q, m, T, s) in reps:
+        a = sw.Lattice(L, q, MODEL[m], T, s, init=sw.SW_INIT_RANDOM)
+        a.sweep(18)
+        alone.append(a.spins.copy())
+        a.close()
+    for lat, sp in zip(lats, alone):
+        assert np.array_equal(lat.spins, sp)
+    b.close()
+
+
+def test_attach_detach_mid_run_keeps_each_chain():
+    """Lattices join and leave a running batch (the serving pattern)."""
+    Tc = 1.0 / math.log(1.0 + math.sqrt(2.0))
+    b = sw.Batch()
+    x = b.add(64, 2, sw.SW_POTTS, Tc, 1, init=sw.SW_INIT_RANDOM)
+    y = b.add(36, 3, sw.SW_POTTS, 0.9, 2, init=sw.SW_INIT_RANDOM)
+    b.sweep(5)
+    z = b.add(100, 6, sw.SW_CLOCK, 0.9, 3, init=sw.SW_INIT_RANDOM)
+    b.sweep(4)
+    b.remove(y)
+    b.sweep(3)
+    ox = Oracle(64, 2, POTTS, Tc, 1, init="random"); ox.sweep(12)
+    oy = Oracle(36, 3, POTTS, 0.9, 2, init="random"); oy.sweep(9)
+    oz = Oracle(100, 6, CLOCK, 0.9, 3, init="random"); oz.sweep(7)
+    assert np.array_equal(x.spins, ox.spins)
+    assert np.array_equal(y.spins, oy.spins)
+    assert np.array_equal(z.spins, oz.spins)
+    y.sweep(2)   # a detached lattice keeps working alone
+    oy.sweep(2)
+    assert np.array_equal(y.spins, oy.spins)
+    y.close()
+    b.close()
+
+
+def test_batch_measure_off_and_labels():
+    Tc = 1.0 / math.log(1.0 + math.sqrt(3.0))
+    b = sw.Batch()
+    sw.sw_batch_set_debug_labels(b.b, 1)
+    lats = [b.add(L, 3, sw.SW_POTTS, Tc, 7 + L, init=sw.SW_INIT_RANDOM) for L in (32, 68, 96)]
+    refs = [Oracle(L, 3, POTTS, Tc, 7 + L, init="random") for L in (32, 68, 96)]
+    b.sweep(2)
+    for lat, ref in zip(lats, refs):
+        ref.sweep(2)
+        assert np.array_equal(lat.labels, ref.labels)
+    sw.sw_batch_set_measure(b.b, 0)
+    b.sweep(5)
+    for lat, ref in zip(lats, refs):
+        ref.sweep(5)
+        assert np.array_equal(lat.spins, ref.spins)
+        assert lat.measure().nmeas == 2
+    b.close()
