@@ -40,6 +40,7 @@ constexpr int kEnergyThreads = 256;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint16_t kCodeFlip = 0x4000;   // closed clock cluster: reflected
 constexpr int kNone = 0x7FFFFFFF;
+constexpr int kRootFlag = 0x40000000;   // parent word of a resolved tile root: flag | code
 
 static_assert(TW == 32 && TH == 32, "the warp-tile layout assumes 32 x 32 tiles");
 static_assert(sizeof(Lattice) % 8 == 0, "lattice descriptors are copied in 8-byte words");
@@ -184,10 +185,9 @@ __global__ void k_init(Lattice lat, int random)
 // ones and write the per-site codes.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kBlockThreads) k_label_tiles(Batch b)
+__global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
 {
     __shared__ int par_all[kTaskWarps][NS];
-    __shared__ uint16_t rcode_all[kTaskWarps][NS];
     __shared__ uint16_t roots_all[kTaskWarps][NS];
     __shared__ unsigned int rowS_all[kTaskWarps][32], rowR_all[kTaskWarps][32], rowD_all[kTaskWarps][32];
     __shared__ unsigned int openw_all[kTaskWarps][32];
@@ -199,7 +199,6 @@ __global__ void __launch_bounds__(kBlockThreads) k_label_tiles(Batch b)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *par = par_all[warp];
-    uint16_t *rcode = rcode_all[warp];
     uint16_t *roots = roots_all[warp];
     unsigned int *rowS = rowS_all[warp], *rowR = rowR_all[warp], *rowD = rowD_all[warp];
     unsigned int *openw = openw_all[warp];
@@ -350,13 +349,17 @@ __global__ void __launch_bounds__(kBlockThreads) k_label_tiles(Batch b)
         // ===== phase B: lane = column, scanline over the rows ================
         const int c = lane;
         const bool cv = c < ncols;
-        const unsigned above_c = ~(FULL >> (31 - c));   // columns > c
-        par[c] = cv ? start_of(rowS[0], c) : c;
+        const unsigned upto_c = FULL >> (31 - c);   // columns <= c
+        unsigned S = rowS[0], R = rowR[0];
+        par[c] = cv ? 31 - __clz(S & upto_c) : c;
         for (int row = 0; row + 1 < nrows; ++row) {
-            const unsigned Sn = rowS[row + 1], D = rowD[row], R = rowR[row], Rn = rowR[row + 1];
+            const unsigned Sn = rowS[row + 1], Rn = rowR[row + 1], D = rowD[row];
             // A vertical bond is implied by its left neighbour column when both
             // rows are joined across that column pair.
             const unsigned E = D & ~((D & R & Rn) << 1);
+            const int base1 = (row + 1) * TW;
+            const int s = cv ? 31 - __clz(Sn & upto_c) : c;   // start of my run in row + 1
+            par[base1 + c] = kNone;
             int cand = kNone;
             if ((E >> c) & 1u) {
                 cand = find_s(par, row * TW + c, NS + 1);
@@ -365,75 +368,93 @@ __global__ void __launch_bounds__(kBlockThreads) k_label_tiles(Batch b)
                     cand = kNone;
                 }
             }
-            // Smallest candidate of my run: inclusive min-scan within runs,
-            // then read it from the run's last lane.
-            const int s = cv ? start_of(Sn, c) : c;
-            const unsigned nxt = Sn & above_c;
-            const int e = cv ? (nxt ? __ffs(nxt) - 1 : ncols) : c + 1;   // run end (exclusive)
-            int v = cand;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int u = __shfl_up_sync(FULL, v, d);
-                if (c - d >= s) v = min(v, u);
-            }
-            int mm = __shfl_sync(FULL, v, e - 1);
-            if (mm == kNone) mm = (row + 1) * TW + s;
+            __syncwarp();
+            // Smallest root touched by my run, collected at the run start's slot.
+            if (cand != kNone) atomicMin(&par[base1 + s], cand);
+            __syncwarp();
+            int mm = par[base1 + s];
+            if (mm == kNone) mm = base1 + s;
             if (cand != kNone && cand != mm && !union_s(par, cand, mm, NS + 1))
                 record_error(lat.st, kErrUnionCap, y0 * L + x0);
-            par[(row + 1) * TW + c] = cv ? mm : (row + 1) * TW + c;
             __syncwarp();
+            par[base1 + c] = mm;
+            __syncwarp();
+            S = Sn;
+            R = Rn;
         }
 
-        // ===== phase C: roots, border components, codes ======================
+        // ===== phase C: roots, border components, draws, codes ================
+        // A site is a root iff its parent word is itself (unions only ever
+        // re-point roots).  Collect the roots in row order.
         int nroots = 0;
         for (int row = 0; row < nrows; ++row) {
             const int x = row * TW + c;
-            int root = x;
-            if (cv) {
-                root = find_s(par, x, NS + 1);
-                if (root < 0) {
-                    record_error(lat.st, kErrFindCap, y0 * L + x0);
-                    root = x;
-                }
-                par[x] = root;
-                // Left and top edges: the bonds into the tile belong to the
-                // neighbouring tiles, so those sites always count as open.
-                const bool open = (row == 0) || (c == 0) || (c == ncols - 1 && ((rc_bits >> row) & 1u)) ||
-                                  (row == nrows - 1 && ((dc_bits >> c) & 1u));
-                if (open) atomicOr(&openw[root >> 5], 1u << (root & 31));
-            }
-            const bool isroot = cv && root == x;
+            const bool isroot = cv && par[x] == x;
             const unsigned bal = __ballot_sync(FULL, isroot);
             if (isroot) roots[nroots + __popc(bal & lanemask_lt)] = (uint16_t)x;
             nroots += __popc(bal);
         }
+        // Components reaching the tile border.  Left and top edges always
+        // count (their bonds belong to the neighbouring tiles); right and
+        // bottom edges count through an active crossing bond.
+        {
+            int site[4];
+            bool want[4];
+            want[0] = cv;                                               // top row, column c
+            site[0] = c;
+            want[1] = c < nrows;                                        // left column, row c
+            site[1] = c * TW;
+            want[2] = c < nrows && ((rc_bits >> c) & 1u);              // right edge, row c
+            site[2] = c * TW + ncols - 1;
+            want[3] = cv && ((dc_bits >> c) & 1u);                     // bottom row, column c
+            site[3] = (nrows - 1) * TW + c;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!want[k]) continue;
+                int root = find_s(par, site[k], NS + 1);
+                if (root < 0) {
+                    record_error(lat.st, kErrFindCap, y0 * L + x0);
+                    continue;
+                }
+                atomicOr(&openw[root >> 5], 1u << (root & 31));
+            }
+        }
         __syncwarp();
+        // Closed roots draw now; open roots join the global union-find.  The
+        // result is stored in the root's own parent word, flagged.
         for (int j = c; j < nroots; j += 32) {
             const int x = roots[j];
             const int g = tile_site(L, bx, by, x);
+            int code;
             if ((openw[x >> 5] >> (x & 31)) & 1u) {
                 const int slot = atomicAdd(&nopen_all[warp], 1);
                 lat.open_list[(size_t)tile * kOpenSlots + slot] = g;
                 lat.label[g] = g;
-                rcode[x] = (uint16_t)x;
+                code = x;
             } else {
                 const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
-                rcode[x] = clock ? (uint16_t)(kCodeClosed | ((u >> 31) ? kCodeFlip : 0))
-                                 : (uint16_t)(kCodeClosed | mulhi_q(u, q));
+                code = clock ? (kCodeClosed | ((u >> 31) ? kCodeFlip : 0)) : (kCodeClosed | mulhi_q(u, q));
                 ++closed_roots;
             }
+            par[x] = kRootFlag | code;
         }
         __syncwarp();
         if (cv) {
             for (int row = 0; row < nrows; ++row) {
                 const size_t site = (size_t)(y0 + row) * L + x0 + c;
-                const int root = par[row * TW + c];
-                uint32_t code = rcode[root];
+                // Follow parents to the flagged root word.
+                int x = row * TW + c;
+                int p = par[x];
+                for (int it = 0; it < NS && !(p & kRootFlag); ++it) {
+                    x = p;
+                    p = par[x];
+                }
+                uint32_t code = (uint32_t)p & 0xFFFFu;
                 if (clock && (code & kCodeClosed)) {
                     const int k0 = valid_state(__ldg(lat.spin + site), q);
                     code = kCodeClosed | (uint32_t)((code & kCodeFlip) ? reflect(k0, m, q) : k0);
                 }
-                if (LABELS && (code & kCodeClosed)) lat.label[site] = tile_site(L, bx, by, root);
+                if (LABELS && (code & kCodeClosed)) lat.label[site] = tile_site(L, bx, by, x);
                 lat.code[site] = (uint16_t)code;
             }
         }
