@@ -73,6 +73,7 @@ struct sw_handle {
     uint32_t *d_thr_tab = nullptr;
     uint16_t *d_code = nullptr;
     int32_t *d_open_list = nullptr, *d_open_count = nullptr;
+    uint8_t *d_open_state = nullptr;
     uint32_t *d_cross = nullptr;
     int tiles_x = 0, tiles_y = 0;
     DevState *d_st = nullptr;
@@ -115,6 +116,7 @@ struct sw_handle {
         lat.code = d_code;
         lat.open_list = d_open_list;
         lat.open_count = d_open_count;
+        lat.open_state = d_open_state;
         lat.cross = d_cross;
         lat.tiles_x = tiles_x;
         lat.tiles_y = tiles_y;
@@ -337,6 +339,7 @@ void free_handle(sw_handle *h)
     if (h->d_code) cudaFree(h->d_code);
     if (h->d_open_list) cudaFree(h->d_open_list);
     if (h->d_open_count) cudaFree(h->d_open_count);
+    if (h->d_open_state) cudaFree(h->d_open_state);
     if (h->d_cross) cudaFree(h->d_cross);
     if (h->d_st) cudaFree(h->d_st);
     if (h->d_ring) cudaFree(h->d_ring);
@@ -419,6 +422,8 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
         return bail(e, "cudaMalloc(open roots)");
     if ((e = cudaMalloc(&h->d_open_count, ntiles * sizeof(int32_t))) != cudaSuccess)
         return bail(e, "cudaMalloc(open counts)");
+    if ((e = cudaMalloc(&h->d_open_state, ntiles * swgb::kOpenSlots)) != cudaSuccess)
+        return bail(e, "cudaMalloc(open states)");
     if ((e = cudaMalloc(&h->d_cross, ntiles * swgb::kCrossWords * sizeof(uint32_t))) != cudaSuccess)
         return bail(e, "cudaMalloc(crossing bonds)");
     if ((e = cudaMalloc(&h->d_ring, sizeof(unsigned long long) * swgb::kRingSlots * h->ncounters)) != cudaSuccess)

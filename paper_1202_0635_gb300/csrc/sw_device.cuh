@@ -41,6 +41,8 @@ struct Lattice {
     int32_t *label;             // L*L words: union-find parents of open tile roots; debug labels
     uint16_t *code;             // L*L per-site codes written by the labeling stage
     int32_t *open_list;         // tiles x kOpenSlots global indices of open tile roots
+                                // (after the flatten stage: their cluster roots)
+    uint8_t *open_state;        // tiles x kOpenSlots new state / reflect flag of each open root's cluster
     int32_t *open_count;        // tiles
     uint32_t *cross;            // tiles x 2 words: active crossing bonds (right edge rows, bottom edge columns)
     int tiles_x, tiles_y;

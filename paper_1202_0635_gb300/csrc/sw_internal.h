@@ -21,9 +21,8 @@ constexpr int kOpenSlots = 128;
 // Crossing-bond words per tile: [0] bit r = right-edge bond of row r,
 // [1] bit c = bottom-edge bond of column c.
 constexpr int kCrossWords = 2;
-// Per-site code: closed component -> kCodeClosed | new state (Potts) or
-// kCodeClosed | kCodeFlip-if-reflected | new state (clock); open component
-// -> tile-local index (row * 32 + column) of its root.
+// Per-site code: closed component -> kCodeClosed | new state; open
+// component -> slot of its root in the tile's open list.
 constexpr uint16_t kCodeClosed = 0x8000;
 
 // Counter rows kept on the device; the host drains them before the ring

@@ -91,13 +91,6 @@ __device__ __forceinline__ unsigned zero_bytes4(unsigned x)
     return (((t >> 7) * 0x00204081u) >> 21) & 0xFu;
 }
 
-// Start column of the run (of right bonds) that contains column c; S holds
-// the run starts of the row and always has bit 0 set.
-__device__ __forceinline__ int start_of(unsigned S, int c)
-{
-    return 31 - __clz(S & (FULL >> (31 - c)));
-}
-
 __device__ __forceinline__ int byte_at(const uint32_t (&w)[8], int c)
 {
     return (int)((w[c >> 2] >> (8 * (c & 3))) & 0xFFu);
@@ -430,7 +423,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                 const int slot = atomicAdd(&nopen_all[warp], 1);
                 lat.open_list[(size_t)tile * kOpenSlots + slot] = g;
                 lat.label[g] = g;
-                code = x;
+                code = slot;
             } else {
                 const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
                 code = clock ? (kCodeClosed | ((u >> 31) ? kCodeFlip : 0)) : (kCodeClosed | mulhi_q(u, q));
@@ -476,12 +469,13 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
 __device__ __forceinline__ int open_root_of(const Lattice &lat, int site, bool &ok)
 {
     const int sy = site / lat.L, sx = site - sy * lat.L;
-    const int code = lat.code[site];   // open site: tile-local index of its root
+    const int code = lat.code[site];   // open site: slot of its root in the tile's open list
     if (code & kCodeClosed) {
         ok = false;
         return site;
     }
-    return tile_site(lat.L, sx / TW, sy / TH, code);
+    const int tile = (sy / TH) * lat.tiles_x + sx / TW;
+    return __ldg(lat.open_list + (size_t)tile * kOpenSlots + code);
 }
 
 __global__ void k_merge(Batch b)
@@ -527,7 +521,9 @@ __global__ void k_merge(Batch b)
 }
 
 // ---------------------------------------------------------------------------
-// k_flatten: every open root -> its cluster root; count cluster roots.
+// k_flatten: every open root -> its cluster root, which draws the cluster's
+// new state (Potts) or reflection flag (clock) into the tile's open-state
+// table; the open list then holds the cluster roots.  Counts cluster roots.
 // One warp per tile.
 // ---------------------------------------------------------------------------
 template <bool MEASURE>
@@ -559,10 +555,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_flatten(Batch b)
         const int cap = lat.L * lat.L + 1;
         const int n = lat.open_count[tile];
         for (int s = lane; s < n; s += 32) {
-            const int r = lat.open_list[(size_t)tile * kOpenSlots + s];
+            const size_t k = (size_t)tile * kOpenSlots + s;
+            const int r = lat.open_list[k];
             const int root = find_root_halving(lat.label, r, cap, lat.st);
             if (root != r) lat.label[r] = root;
             else ++roots;
+            const uint32_t u = draw4(lat, (uint32_t)root, s_t, kTagState).x;
+            lat.open_state[k] = lat.clock ? (uint8_t)(u >> 31) : (uint8_t)mulhi_q(u, lat.q);
+            lat.open_list[k] = root;
         }
     }
     flush();
@@ -604,8 +604,8 @@ __device__ void finish_sweep(const Batch &b)
 template <bool MEASURE, bool LABELS>
 __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
 {
-    __shared__ unsigned char tab_all[kTaskWarps][NS];
-    __shared__ int rootg_all[LABELS ? kTaskWarps : 1][LABELS ? NS : 1];
+    __shared__ __align__(16) unsigned char tab_all[kTaskWarps][kOpenSlots];
+    __shared__ int rootg_all[LABELS ? kTaskWarps : 1][LABELS ? kOpenSlots : 1];
     __shared__ unsigned int hist_state[SW_MAX_Q + 1];
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
@@ -652,69 +652,68 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
         const int by = have ? tile / lat.tiles_x : 0, bx = have ? tile - by * lat.tiles_x : 0;
         const int x0 = bx * TW, y0 = by * TH;
         const int ncols = have ? min(TW, L - x0) : 0, nrows = have ? min(TH, L - y0) : 0;
-        const bool rv = r < nrows;
-        const size_t rowbase = (size_t)(y0 + r) * L + x0;
-
-        // Row codes (and old states for the clock reflection) first, so the
-        // loads overlap the root lookups below.
+        // Lane -> 4 consecutive sites: columns cq..cq+3 of row 4 * step + rsub,
+        // so every warp access covers whole 32-byte sectors of 4 rows.
+        const int cq = (r & 7) * 4, rsub = r >> 3;
         uint2 cw[8];
         uint32_t sw[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const bool v = rv && 4 * k < ncols;
-            cw[k] = v ? reinterpret_cast<const uint2 *>(lat.code + rowbase)[k] : make_uint2(0u, 0u);
-            sw[k] = (clock && v) ? reinterpret_cast<const uint32_t *>(lat.spin + rowbase)[k] : 0u;
+            const int row = 4 * k + rsub;
+            const bool v = row < nrows && cq < ncols;
+            const size_t site0 = (size_t)(y0 + row) * L + x0 + cq;
+            cw[k] = v ? *reinterpret_cast<const uint2 *>(lat.code + site0) : make_uint2(0u, 0u);
+            sw[k] = (clock && v) ? *reinterpret_cast<const uint32_t *>(lat.spin + site0) : 0u;
         }
-        const int n = have ? lat.open_count[tile] : 0;
-        for (int s = r; s < n; s += 32) {
-            const int rg = lat.open_list[(size_t)tile * kOpenSlots + s];
-            const int g = find_root_ro(lat.label, rg, L * L + 1, lat.st);
-            const uint32_t u = draw4(lat, (uint32_t)g, ctx.t, kTagState).x;
-            const int ry = rg / L, rx = rg - ry * L;
-            const int loc = (ry - y0) * TW + (rx - x0);
-            tab[loc] = clock ? (unsigned char)(u >> 31) : (unsigned char)mulhi_q(u, q);
-            if (LABELS) rootg_all[LABELS ? warp : 0][LABELS ? loc : 0] = g;
+        // The tile's open-state table (kOpenSlots bytes) into shared memory.
+        if (have) {
+            const size_t k0 = (size_t)tile * kOpenSlots;
+            reinterpret_cast<uint32_t *>(tab)[r] = __ldg(reinterpret_cast<const uint32_t *>(lat.open_state + k0) + r);
+            if (LABELS)
+                for (int s = r; s < kOpenSlots; s += 32) rootg_all[LABELS ? warp : 0][LABELS ? s : 0] = lat.open_list[k0 + s];
         }
         __syncwarp();
 
-        if (rv) {
-            uint32_t *dst = reinterpret_cast<uint32_t *>(lat.spin + rowbase);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                uint32_t word = 0;
+        for (int k = 0; k < 8; ++k) {
+            const int row = 4 * k + rsub;
+            if (!(row < nrows && cq < ncols)) continue;
+            const size_t site0 = (size_t)(y0 + row) * L + x0 + cq;
+            uint32_t word = 0;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const uint32_t code = ((h < 2) ? (cw[k].x >> (16 * h)) : (cw[k].y >> (16 * (h - 2)))) & 0xFFFFu;
-                    int ns;
-                    if (code & kCodeClosed) {
-                        ns = (int)(code & 0x7Fu);
-                    } else if (clock) {
-                        const int k0 = valid_state((int)((sw[k] >> (8 * h)) & 0xFFu), q);
-                        ns = tab[code] ? reflect(k0, m, q) : k0;
-                    } else {
-                        ns = tab[code];
-                    }
-                    const bool v = 4 * k + h < ncols;
-                    if (MEASURE && q <= 8 && v) {
-                        const unsigned long long one = 1ull << (16 * (ns & 3));
-                        if (ns < 4) cnt_lo += one;
-                        else cnt_hi += one;
-                    }
-                    if (LABELS && v && !(code & kCodeClosed))
-                        lat.label[rowbase + 4 * k + h] = rootg_all[LABELS ? warp : 0][LABELS ? code : 0];
-                    word |= (uint32_t)(ns & 0xFF) << (8 * h);
+            for (int h = 0; h < 4; ++h) {
+                const uint32_t code = ((h < 2) ? (cw[k].x >> (16 * h)) : (cw[k].y >> (16 * (h - 2)))) & 0xFFFFu;
+                int ns;
+                if (code & kCodeClosed) {
+                    ns = (int)(code & 0x7Fu);
+                } else if (clock) {
+                    const int k0 = valid_state((int)((sw[k] >> (8 * h)) & 0xFFu), q);
+                    ns = tab[code] ? reflect(k0, m, q) : k0;
+                } else {
+                    ns = tab[code];
                 }
-                if (4 * k < ncols) dst[k] = word;
+                if (MEASURE && q <= 8) {
+                    const unsigned long long one = 1ull << (16 * (ns & 3));
+                    if (ns < 4) cnt_lo += one;
+                    else cnt_hi += one;
+                }
+                if (LABELS && !(code & kCodeClosed))
+                    lat.label[site0 + h] = rootg_all[LABELS ? warp : 0][LABELS ? code : 0];
+                word |= (uint32_t)(ns & 0xFF) << (8 * h);
             }
+            *reinterpret_cast<uint32_t *>(lat.spin + site0) = word;
         }
         if (MEASURE && q > 8) {
             // Many states: warp-aggregated shared histogram, site by site.
 #pragma unroll 1
-            for (int c = 0; c < 32; ++c) {
-                const bool v = rv && c < ncols;
-                int ns = 0;
-                if (v) ns = (int)(lat.spin[rowbase + c]);
-                add_hist_any(hist_state, ns, v && ns >= 0 && ns < q);
+            for (int k = 0; k < 8; ++k) {
+                const int row = 4 * k + rsub;
+                const bool v = row < nrows && cq < ncols;
+                const size_t site0 = (size_t)(y0 + row) * L + x0 + cq;
+                for (int h = 0; h < 4; ++h) {
+                    const int ns = v ? (int)lat.spin[site0 + h] : 0;
+                    add_hist_any(hist_state, ns, v && ns >= 0 && ns < q);
+                }
             }
         }
         __syncwarp();
