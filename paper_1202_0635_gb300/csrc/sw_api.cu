@@ -129,7 +129,7 @@ struct sw_handle {
     }
 
     int ntiles() const { return tiles_x * tiles_y; }
-    int ntasks() const { return (ntiles() + swgb::kTaskWarps - 1) / swgb::kTaskWarps; }
+    int ntasks() const { return ntiles(); }
     long long nmerge() const { return (long long)L * (tiles_x + tiles_y); }
 
     Batch self_batch() const

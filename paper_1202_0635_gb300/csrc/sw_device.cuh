@@ -54,12 +54,11 @@ struct Lattice {
 };
 
 // A set of lattices swept together; a single lattice is a batch of one.
-// Tiles are grouped into block tasks of kTaskWarps tiles of one lattice, so
-// every block works on one lattice at a time.
+// One block task is one tile of one lattice, processed by kTaskWarps warps.
 constexpr int kTaskWarps = 4;
 struct Batch {
     const Lattice *lat;            // [nrep] descriptors (device memory)
-    const int *task_off;           // [nrep + 1] prefix sums of ceil(tiles / kTaskWarps)
+    const int *task_off;           // [nrep + 1] prefix sums of the lattices' tile counts
     const long long *merge_off;    // [nrep + 1] prefix sums of L * (tiles_x + tiles_y)
     unsigned int *ticket;          // blocks finished in the sweep's last kernel
     int nrep;

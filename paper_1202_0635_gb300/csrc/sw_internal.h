@@ -10,17 +10,21 @@
 
 namespace swgb {
 
-// Tile of the labeling stage: 32 x 32 sites, one warp per tile, lane r
-// owning row r of the tile as 32-bit masks.
-constexpr int kTileW = 32;
-constexpr int kTileH = 32;
+// Tiles: a block labels one 64 x 64 tile (the unit of global work) with
+// four warps, each owning a 32 x 32 quadrant whose lane r holds row r as
+// 32-bit masks.  Quadrant borders inside the tile are merged in shared
+// memory; only components reaching the tile border go global.
+constexpr int kTileW = 64;
+constexpr int kTileH = 64;
+constexpr int kQuad = 32;
 constexpr int kTileSites = kTileW * kTileH;
+static_assert(kTaskWarps == (kTileW / kQuad) * (kTileH / kQuad), "one warp per quadrant");
 // A component that reaches a tile border ("open") owns a border site, so a
-// tile has at most 2 * (W + H) - 4 = 124 open components.
-constexpr int kOpenSlots = 128;
-// Crossing-bond words per tile: [0] bit r = right-edge bond of row r,
-// [1] bit c = bottom-edge bond of column c.
-constexpr int kCrossWords = 2;
+// tile has at most 2 * (W + H) - 4 = 252 open components.
+constexpr int kOpenSlots = 256;
+// Crossing-bond words per tile: [0], [1] bit r = right-edge bond of row
+// 32 * w + r; [2], [3] bit c = bottom-edge bond of column 32 * w + c.
+constexpr int kCrossWords = 4;
 // Per-site code: closed component -> kCodeClosed | new state; open
 // component -> slot of its root in the tile's open list.
 constexpr uint16_t kCodeClosed = 0x8000;

@@ -1,10 +1,10 @@
 // sw_kernels.cu -- the kernels of one Swendsen-Wang sweep on sm_103a.
 //
 // One sweep (Komura & Okabe, arXiv:1202.0635, Sec. 2 steps (i)-(viii);
-// clock model: Sec. 4 embedded clusters) is four launches over 32 x 32
+// clock model: Sec. 4 embedded clusters) is four launches over the 64 x 64
 // tiles of every lattice of a batch (a single lattice is a batch of one).
-// A warp owns a tile; a block owns kTaskWarps tiles of one lattice at a
-// time ("task"), so per-lattice counters reduce per block.
+// A block owns one tile of one lattice at a time ("task"); each of its four
+// warps owns a 32 x 32 quadrant, so per-lattice counters reduce per block.
 //
 //   k_label_tiles  bonds of every site (Sec. 2 (ii)): equal-neighbour masks
 //                  from packed byte compares, Philox draws against the
@@ -34,7 +34,7 @@ namespace swgb {
 
 namespace {
 
-constexpr int TW = kTileW, TH = kTileH, NS = kTileSites;
+constexpr int TW = kTileW, TH = kTileH, NS = kTileSites, QW = kQuad;
 constexpr int kBlockThreads = kTaskWarps * 32;
 constexpr int kEnergyThreads = 256;
 constexpr unsigned FULL = 0xffffffffu;
@@ -42,7 +42,8 @@ constexpr uint16_t kCodeFlip = 0x4000;   // closed clock cluster: reflected
 constexpr int kNone = 0x7FFFFFFF;
 constexpr int kRootFlag = 0x40000000;   // parent word of a resolved tile root: flag | code
 
-static_assert(TW == 32 && TH == 32, "the warp-tile layout assumes 32 x 32 tiles");
+static_assert(QW == 32, "a warp quadrant is 32 x 32: lane r owns row r as a 32-bit mask");
+static_assert(TW == 2 * QW && TH == 2 * QW, "a tile is 2 x 2 quadrants");
 static_assert(sizeof(Lattice) % 8 == 0, "lattice descriptors are copied in 8-byte words");
 
 __device__ __forceinline__ unsigned long long read_u64(const unsigned long long *p)
@@ -78,10 +79,10 @@ __device__ __forceinline__ void load_lattice(Lattice *dst, const Lattice *src)
     for (int i = threadIdx.x; i < (int)(sizeof(Lattice) / 8); i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-// Global site index of tile-local index loc (row * 32 + column) in tile (bx, by).
+// Global site index of tile-local node loc (row * 64 + column) in tile (bx, by).
 __device__ __forceinline__ int tile_site(int L, int bx, int by, int loc)
 {
-    return (by * TH + (loc >> 5)) * L + bx * TW + (loc & 31);
+    return (by * TH + loc / TW) * L + bx * TW + (loc % TW);
 }
 
 // Bit k of the result is set iff byte k of x is zero.
@@ -168,33 +169,34 @@ __global__ void k_init(Lattice lat, int random)
 // ---------------------------------------------------------------------------
 // k_label_tiles
 //
-// Phase A (lane r = row r): bond masks of the row.  Phase B (lane c =
-// column c): a scanline over the rows.  Every site's parent word holds the
-// label of its run; a run of row y+1 takes the smallest root among the
-// runs of row y it touches (segmented shuffle min-scan over the run's
-// lanes), and the other touched roots are linked under it.  Roots thus stay
-// the smallest site index of their component.  Phase C: resolve every
-// site's root, mark components that reach the tile border, draw the closed
-// ones and write the per-site codes.
+// Per quadrant (warp):  phase A (lane r = row r) bond masks of the row;
+// phase B (lane c = column c) a scanline over the rows: every site's parent
+// word holds its run's label, a run of row y+1 takes the smallest root among
+// the runs of row y it touches (atomicMin at the run start's slot) and the
+// other touched roots are linked under it.  Tile nodes are numbered
+// row * 64 + column, which orders them like global site indices, so roots
+// stay the smallest site of their component.  Then the block joins the
+// quadrants across their inner borders, finds the roots, marks components
+// that reach the tile border, draws the closed ones and writes the codes.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS>
 __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
 {
-    __shared__ int par_all[kTaskWarps][NS];
-    __shared__ uint16_t roots_all[kTaskWarps][NS];
+    __shared__ int par[NS];
+    __shared__ uint16_t roots_all[kTaskWarps][QW * QW];
     __shared__ unsigned int rowS_all[kTaskWarps][32], rowR_all[kTaskWarps][32], rowD_all[kTaskWarps][32];
-    __shared__ unsigned int openw_all[kTaskWarps][32];
-    __shared__ int nopen_all[kTaskWarps];
+    __shared__ unsigned int openw[NS / 32];
+    __shared__ int s_nopen;
+    __shared__ unsigned int s_cross[kCrossWords];
     __shared__ unsigned int hist_class[SW_MAX_CLOCK_Q / 2 + 2];
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *par = par_all[warp];
+    const int qx = warp & 1, qy = warp >> 1;
     uint16_t *roots = roots_all[warp];
     unsigned int *rowS = rowS_all[warp], *rowR = rowR_all[warp], *rowD = rowD_all[warp];
-    unsigned int *openw = openw_all[warp];
     const unsigned lanemask_lt = (1u << lane) - 1u;
 
     unsigned int active = 0, closed_roots = 0, unequal = 0, pairs = 0;
@@ -233,21 +235,31 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
             __syncthreads();
             cur = rep;
         }
-        const int tile = (task - __ldg(b.task_off + rep)) * kTaskWarps + warp;
-        if (tile >= lat.tiles_x * lat.tiles_y) continue;   // whole warp
+        const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
         const bool clock = lat.clock != 0;
         const unsigned long long t = ctx.t;
         const int m = ctx.m;
         const uint32_t thr = lat.thr;
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
-        const int x0 = bx * TW, y0 = by * TH;
-        const int ncols = min(TW, L - x0), nrows = min(TH, L - y0);
-        const unsigned V = ncols == 32 ? FULL : ((1u << ncols) - 1u);
-        unsigned rc_bits, dc_bits;
+        const int X0 = bx * TW, Y0 = by * TH;
+        const int tw = min(TW, L - X0), th = min(TH, L - Y0);          // valid extent of the tile
+        const int x0 = X0 + QW * qx, y0 = Y0 + QW * qy;                // my quadrant
+        const int ncols = max(0, min(QW, tw - QW * qx));
+        const int nrows = max(0, min(QW, th - QW * qy));
+        const bool qa = ncols > 0 && nrows > 0;                        // quadrant has sites (warp-uniform)
+        const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
+        const bool ext_right = QW * qx + ncols == tw;                   // my right edge is the tile's
+        const bool ext_bottom = QW * qy + nrows == th;
+        const int nb = (QW * qy) * TW + QW * qx;                        // node of my quadrant's corner
+        unsigned rc_bits = 0, dc_bits = 0;
+
+        for (int i = threadIdx.x; i < NS / 32; i += blockDim.x) openw[i] = 0u;
+        if (threadIdx.x == 0) s_nopen = 0;
+        if (threadIdx.x < kCrossWords) s_cross[threadIdx.x] = 0u;
 
         // ===== phase A: lane = row ==========================================
-        {
+        if (qa) {
             const int r = lane;
             const bool rv = r < nrows;
             const int y = y0 + r;
@@ -328,91 +340,107 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                     }
                 }
             }
-            const unsigned Rint = R & (V >> 1);   // both ends inside the tile
+            const unsigned Rint = R & (V >> 1);   // both ends inside the quadrant
             rowS[r] = rv ? (V & ~(Rint << 1)) : 0u;
             rowR[r] = Rint;
             rowD[r] = (r + 1 < nrows) ? D : 0u;
-            rc_bits = __ballot_sync(FULL, rv && ((R >> (ncols - 1)) & 1u));   // right-edge crossing bonds
-            dc_bits = __shfl_sync(FULL, D, nrows - 1);                       // bottom-edge crossing bonds
-            openw[r] = 0u;
-            if (r == 0) nopen_all[warp] = 0;
-        }
-        __syncwarp();
+            rc_bits = __ballot_sync(FULL, rv && ((R >> (ncols - 1)) & 1u));   // bonds leaving the right edge
+            dc_bits = __shfl_sync(FULL, D, nrows - 1);                       // bonds leaving the bottom edge
+            __syncwarp();
 
-        // ===== phase B: lane = column, scanline over the rows ================
+            // ===== phase B: lane = column, scanline over the rows ============
+            const int c = lane;
+            const bool cv = c < ncols;
+            const unsigned upto_c = FULL >> (31 - c);   // columns <= c
+            unsigned S = rowS[0], Rr = rowR[0];
+            par[nb + c] = nb + (cv ? 31 - __clz(S & upto_c) : c);
+            for (int row = 0; row + 1 < nrows; ++row) {
+                const unsigned Sn = rowS[row + 1], Rn = rowR[row + 1], D2 = rowD[row];
+                // A vertical bond is implied by its left neighbour column when
+                // both rows are joined across that column pair.
+                const unsigned E = D2 & ~((D2 & Rr & Rn) << 1);
+                const int base1 = nb + (row + 1) * TW;
+                const int s = cv ? 31 - __clz(Sn & upto_c) : c;   // start of my run in row + 1
+                par[base1 + c] = kNone;
+                int cand = kNone;
+                if ((E >> c) & 1u) {
+                    cand = find_s(par, nb + row * TW + c, NS + 1);
+                    if (cand < 0) {
+                        record_error(lat.st, kErrFindCap, Y0 * L + X0);
+                        cand = kNone;
+                    }
+                }
+                __syncwarp();
+                // Smallest root touched by my run, collected at the run start's slot.
+                if (cand != kNone) atomicMin(&par[base1 + s], cand);
+                __syncwarp();
+                int mm = par[base1 + s];
+                if (mm == kNone) mm = base1 + s;
+                if (cand != kNone && cand != mm && !union_s(par, cand, mm, NS + 1))
+                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
+                __syncwarp();
+                par[base1 + c] = mm;
+                __syncwarp();
+                S = Sn;
+                Rr = Rn;
+            }
+        }
+        __syncthreads();
+
+        // ===== join the quadrants across their inner borders ==================
+        if (qa) {
+            if (!ext_right && lane < nrows && ((rc_bits >> lane) & 1u))
+                if (!union_s(par, nb + lane * TW + QW - 1, nb + lane * TW + QW, NS + 1))
+                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
+            if (!ext_bottom && lane < ncols && ((dc_bits >> lane) & 1u))
+                if (!union_s(par, nb + (QW - 1) * TW + lane, nb + QW * TW + lane, NS + 1))
+                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
+        }
+        __syncthreads();
+
+        // ===== roots, tile-border components, draws, codes ====================
         const int c = lane;
         const bool cv = c < ncols;
-        const unsigned upto_c = FULL >> (31 - c);   // columns <= c
-        unsigned S = rowS[0], R = rowR[0];
-        par[c] = cv ? 31 - __clz(S & upto_c) : c;
-        for (int row = 0; row + 1 < nrows; ++row) {
-            const unsigned Sn = rowS[row + 1], Rn = rowR[row + 1], D = rowD[row];
-            // A vertical bond is implied by its left neighbour column when both
-            // rows are joined across that column pair.
-            const unsigned E = D & ~((D & R & Rn) << 1);
-            const int base1 = (row + 1) * TW;
-            const int s = cv ? 31 - __clz(Sn & upto_c) : c;   // start of my run in row + 1
-            par[base1 + c] = kNone;
-            int cand = kNone;
-            if ((E >> c) & 1u) {
-                cand = find_s(par, row * TW + c, NS + 1);
-                if (cand < 0) {
-                    record_error(lat.st, kErrFindCap, y0 * L + x0);
-                    cand = kNone;
-                }
-            }
-            __syncwarp();
-            // Smallest root touched by my run, collected at the run start's slot.
-            if (cand != kNone) atomicMin(&par[base1 + s], cand);
-            __syncwarp();
-            int mm = par[base1 + s];
-            if (mm == kNone) mm = base1 + s;
-            if (cand != kNone && cand != mm && !union_s(par, cand, mm, NS + 1))
-                record_error(lat.st, kErrUnionCap, y0 * L + x0);
-            __syncwarp();
-            par[base1 + c] = mm;
-            __syncwarp();
-            S = Sn;
-            R = Rn;
-        }
-
-        // ===== phase C: roots, border components, draws, codes ================
-        // A site is a root iff its parent word is itself (unions only ever
-        // re-point roots).  Collect the roots in row order.
         int nroots = 0;
-        for (int row = 0; row < nrows; ++row) {
-            const int x = row * TW + c;
-            const bool isroot = cv && par[x] == x;
-            const unsigned bal = __ballot_sync(FULL, isroot);
-            if (isroot) roots[nroots + __popc(bal & lanemask_lt)] = (uint16_t)x;
-            nroots += __popc(bal);
-        }
-        // Components reaching the tile border.  Left and top edges always
-        // count (their bonds belong to the neighbouring tiles); right and
-        // bottom edges count through an active crossing bond.
-        {
+        if (qa) {
+            // A node is a root iff its parent word is itself (unions only ever
+            // re-point roots).  Collect my quadrant's roots in row order.
+            for (int row = 0; row < nrows; ++row) {
+                const int x = nb + row * TW + c;
+                const bool isroot = cv && par[x] == x;
+                const unsigned bal = __ballot_sync(FULL, isroot);
+                if (isroot) roots[nroots + __popc(bal & lanemask_lt)] = (uint16_t)x;
+                nroots += __popc(bal);
+            }
+            // Components reaching the tile border.  Left and top edges always
+            // count (their bonds belong to the neighbouring tiles); right and
+            // bottom edges count through an active crossing bond.
             int site[4];
             bool want[4];
-            want[0] = cv;                                               // top row, column c
-            site[0] = c;
-            want[1] = c < nrows;                                        // left column, row c
-            site[1] = c * TW;
-            want[2] = c < nrows && ((rc_bits >> c) & 1u);              // right edge, row c
-            site[2] = c * TW + ncols - 1;
-            want[3] = cv && ((dc_bits >> c) & 1u);                     // bottom row, column c
-            site[3] = (nrows - 1) * TW + c;
+            want[0] = qy == 0 && cv;                                       // top row
+            site[0] = nb + c;
+            want[1] = qx == 0 && c < nrows;                                // left column
+            site[1] = nb + c * TW;
+            want[2] = ext_right && c < nrows && ((rc_bits >> c) & 1u);     // right edge, row c
+            site[2] = nb + c * TW + ncols - 1;
+            want[3] = ext_bottom && cv && ((dc_bits >> c) & 1u);           // bottom edge, column c
+            site[3] = nb + (nrows - 1) * TW + c;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (!want[k]) continue;
-                int root = find_s(par, site[k], NS + 1);
+                const int root = find_s(par, site[k], NS + 1);
                 if (root < 0) {
-                    record_error(lat.st, kErrFindCap, y0 * L + x0);
+                    record_error(lat.st, kErrFindCap, Y0 * L + X0);
                     continue;
                 }
                 atomicOr(&openw[root >> 5], 1u << (root & 31));
             }
+            if (lane == 0) {
+                if (ext_right) atomicOr(&s_cross[qy], rc_bits);
+                if (ext_bottom) atomicOr(&s_cross[2 + qx], dc_bits);
+            }
         }
-        __syncwarp();
+        __syncthreads();
         // Closed roots draw now; open roots join the global union-find.  The
         // result is stored in the root's own parent word, flagged.
         for (int j = c; j < nroots; j += 32) {
@@ -420,7 +448,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
             const int g = tile_site(L, bx, by, x);
             int code;
             if ((openw[x >> 5] >> (x & 31)) & 1u) {
-                const int slot = atomicAdd(&nopen_all[warp], 1);
+                const int slot = atomicAdd(&s_nopen, 1);
                 lat.open_list[(size_t)tile * kOpenSlots + slot] = g;
                 lat.label[g] = g;
                 code = slot;
@@ -431,12 +459,12 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
             }
             par[x] = kRootFlag | code;
         }
-        __syncwarp();
-        if (cv) {
+        __syncthreads();
+        if (qa && cv) {
             for (int row = 0; row < nrows; ++row) {
                 const size_t site = (size_t)(y0 + row) * L + x0 + c;
                 // Follow parents to the flagged root word.
-                int x = row * TW + c;
+                int x = nb + row * TW + c;
                 int p = par[x];
                 for (int it = 0; it < NS && !(p & kRootFlag); ++it) {
                     x = p;
@@ -451,12 +479,9 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                 lat.code[site] = (uint16_t)code;
             }
         }
-        if (lane == 0) {
-            lat.open_count[tile] = nopen_all[warp];
-            lat.cross[(size_t)tile * kCrossWords + 0] = rc_bits;
-            lat.cross[(size_t)tile * kCrossWords + 1] = dc_bits;
-        }
-        __syncwarp();
+        if (threadIdx.x == 0) lat.open_count[tile] = s_nopen;
+        if (threadIdx.x < kCrossWords) lat.cross[(size_t)tile * kCrossWords + threadIdx.x] = s_cross[threadIdx.x];
+        __syncthreads();
     }
     flush();
 }
@@ -497,7 +522,7 @@ __global__ void k_merge(Batch b)
         if (kk < nright) {
             const int y = (int)(kk / ncol), c = (int)(kk % ncol);
             const int tile = (y / TH) * ncol + c;
-            if (!((__ldg(lat.cross + (size_t)tile * kCrossWords) >> (y % TH)) & 1u)) continue;
+            if (!((__ldg(lat.cross + (size_t)tile * kCrossWords + ((y % TH) >> 5)) >> (y & 31)) & 1u)) continue;
             const int x = min((c + 1) * TW, L) - 1;
             i = y * L + x;
             j = y * L + (x + 1 == L ? 0 : x + 1);
@@ -505,7 +530,7 @@ __global__ void k_merge(Batch b)
             const long long k2 = kk - nright;
             const int rr = (int)(k2 / L), x = (int)(k2 % L);
             const int tile = rr * ncol + x / TW;
-            if (!((__ldg(lat.cross + (size_t)tile * kCrossWords + 1) >> (x % TW)) & 1u)) continue;
+            if (!((__ldg(lat.cross + (size_t)tile * kCrossWords + 2 + ((x % TW) >> 5)) >> (x & 31)) & 1u)) continue;
             const int y = min((rr + 1) * TH, L) - 1;
             i = y * L + x;
             j = (y + 1 == L ? 0 : y + 1) * L + x;
@@ -532,7 +557,6 @@ __global__ void __launch_bounds__(kBlockThreads) k_flatten(Batch b)
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
     __shared__ unsigned long long s_t;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned int roots = 0;
     int cur = -1;
     auto flush = [&]() {
@@ -550,11 +574,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_flatten(Batch b)
             __syncthreads();
             cur = rep;
         }
-        const int tile = (task - __ldg(b.task_off + rep)) * kTaskWarps + warp;
-        if (tile >= lat.tiles_x * lat.tiles_y) continue;
+        const int tile = task - __ldg(b.task_off + rep);
         const int cap = lat.L * lat.L + 1;
         const int n = lat.open_count[tile];
-        for (int s = lane; s < n; s += 32) {
+        for (int s = threadIdx.x; s < n; s += blockDim.x) {
             const size_t k = (size_t)tile * kOpenSlots + s;
             const int r = lat.open_list[k];
             const int root = find_root_halving(lat.label, r, cap, lat.st);
@@ -599,19 +622,19 @@ __device__ void finish_sweep(const Batch &b)
 
 // ---------------------------------------------------------------------------
 // k_flip_tiles: new states of open clusters, all spin writes, state counts.
-// One warp per tile; lane r writes row r.
+// One block per tile, one warp per quadrant.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS>
 __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
 {
-    __shared__ __align__(16) unsigned char tab_all[kTaskWarps][kOpenSlots];
-    __shared__ int rootg_all[LABELS ? kTaskWarps : 1][LABELS ? kOpenSlots : 1];
+    __shared__ __align__(16) unsigned char tab[kOpenSlots];
+    __shared__ int rootg[LABELS ? kOpenSlots : 1];
     __shared__ unsigned int hist_state[SW_MAX_Q + 1];
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
     const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
-    unsigned char *tab = tab_all[warp];
+    const int qx = warp & 1, qy = warp >> 1;
     // q <= 8: state counts of this lane, 16 bits per state (states 0-3, 4-7).
     unsigned long long cnt_lo = 0, cnt_hi = 0;
     int cur = -1;
@@ -644,14 +667,15 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
             __syncthreads();
             cur = rep;
         }
-        const int tile = (task - __ldg(b.task_off + rep)) * kTaskWarps + warp;
-        const bool have = tile < lat.tiles_x * lat.tiles_y;
+        const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
         const bool clock = lat.clock != 0;
         const int m = ctx.m;
-        const int by = have ? tile / lat.tiles_x : 0, bx = have ? tile - by * lat.tiles_x : 0;
-        const int x0 = bx * TW, y0 = by * TH;
-        const int ncols = have ? min(TW, L - x0) : 0, nrows = have ? min(TH, L - y0) : 0;
+        const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
+        const int X0 = bx * TW, Y0 = by * TH;
+        const int x0 = X0 + QW * qx, y0 = Y0 + QW * qy;                 // my quadrant
+        const int ncols = max(0, min(QW, min(TW, L - X0) - QW * qx));
+        const int nrows = max(0, min(QW, min(TH, L - Y0) - QW * qy));
         // Lane -> 4 consecutive sites: columns cq..cq+3 of row 4 * step + rsub,
         // so every warp access covers whole 32-byte sectors of 4 rows.
         const int cq = (r & 7) * 4, rsub = r >> 3;
@@ -666,13 +690,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
             sw[k] = (clock && v) ? *reinterpret_cast<const uint32_t *>(lat.spin + site0) : 0u;
         }
         // The tile's open-state table (kOpenSlots bytes) into shared memory.
-        if (have) {
+        {
             const size_t k0 = (size_t)tile * kOpenSlots;
-            reinterpret_cast<uint32_t *>(tab)[r] = __ldg(reinterpret_cast<const uint32_t *>(lat.open_state + k0) + r);
+            for (int i = threadIdx.x; i < kOpenSlots / 4; i += blockDim.x)
+                reinterpret_cast<uint32_t *>(tab)[i] = __ldg(reinterpret_cast<const uint32_t *>(lat.open_state + k0) + i);
             if (LABELS)
-                for (int s = r; s < kOpenSlots; s += 32) rootg_all[LABELS ? warp : 0][LABELS ? s : 0] = lat.open_list[k0 + s];
+                for (int s = threadIdx.x; s < kOpenSlots; s += blockDim.x) rootg[LABELS ? s : 0] = lat.open_list[k0 + s];
         }
-        __syncwarp();
+        __syncthreads();
 
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -698,7 +723,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
                     else cnt_hi += one;
                 }
                 if (LABELS && !(code & kCodeClosed))
-                    lat.label[site0 + h] = rootg_all[LABELS ? warp : 0][LABELS ? code : 0];
+                    lat.label[site0 + h] = rootg[LABELS ? code : 0];
                 word |= (uint32_t)(ns & 0xFF) << (8 * h);
             }
             *reinterpret_cast<uint32_t *>(lat.spin + site0) = word;
@@ -716,7 +741,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();   // the next tile reuses the open-state table
     }
     flush();
     finish_sweep<MEASURE>(b);
