@@ -160,6 +160,63 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(sw, torch, dev, steps):
+    """256 independent replicas of uneven L, model and T (seeded recipe) in one
+    batched launch sequence per sweep, against a loop of plain per-replica
+    sweeps on the same GPU.  Sigma L^2 ~ 6e7 sites: inputs exceed the L2."""
+    from paper_1202_0635_gb300 import workloads
+    reps = workloads.batched_replicas(256, seed=1)
+    stream = torch.cuda.Stream(device=dev)
+    b = sw.Batch(stream=stream.cuda_stream)
+    for r in reps:
+        b.add(r["L"], r["q"], r["model"], r["T"], r["seed"], init=sw.SW_INIT_RANDOM)
+    sw.sw_batch_set_graph(b.b, 1)
+    shape = sw.sw_batch_autotune(b.b, 1)
+    b.sweep(5)
+    sw.sw_batch_synchronize(b.b)
+    sites = sum(r["L"] * r["L"] for r in reps)
+    nb = max(5, min(steps, 30))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.sweep(nb)
+    e1.record(stream)
+    e1.synchronize()
+    tb = e0.elapsed_time(e1) / nb
+    npl = max(3, min(steps, 10))
+    for lat in b.lattices:   # warm the per-replica graphs
+        sw.sw_set_graph(lat.h, 1)
+        lat.sweep(1)
+    e0.record(stream)
+    for _ in range(npl):
+        for lat in b.lattices:
+            lat.sweep(1)
+    e1.record(stream)
+    e1.synchronize()
+    tp = e0.elapsed_time(e1) / npl
+    b.close()
+    return {"replicas": len(reps), "sites": sites, "launch_shape": shape,
+            "ms_per_sweep": tb, "ns_per_flip": tb * 1e6 / sites, "sweeps_per_s": len(reps) / (tb * 1e-3),
+            "plain_loop_ms_per_sweep": tp, "plain_ns_per_flip": tp * 1e6 / sites,
+            "plain_sweeps_per_s": len(reps) / (tp * 1e-3), "speedup_vs_plain_loop": tp / tb,
+            "l2": "no flush: the replicas' spins and codes (~%.0f MB) exceed the L2" % (sites * 3 / 1e6)}
+
+
+def run_served(jobs_n=300, sweep_scale=0.25):
+    """Poisson(200/s) job stream (seeded recipe) through the continuous-
+    batching server, 120 GB budget; sweeps per job scaled by sweep_scale so
+    the default benchmark stays short."""
+    from paper_1202_0635_gb300 import serve, workloads
+    jobs = workloads.served_jobs(jobs_n, rate=200.0, seed=7, sweep_scale=sweep_scale)
+    backend = serve.GpuBackend()
+    srv = serve.Server(backend, budget_bytes=120e9, max_chunk=16)
+    makespan = srv.run(jobs)
+    backend.shutdown()
+    out = serve.summary(jobs, srv.results, makespan)
+    out.update({"rate_per_s": 200.0, "budget_gb": 120.0, "sweep_scale": sweep_scale,
+                "engine_steps": srv.steps, "peak_resident_jobs": srv.peak_resident})
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_1202_0635_gb300 as sw
@@ -282,6 +339,13 @@ def run_ours(args, world, rank, local):
     e2e_value = e2e_s * 1e9 / (ne2e * N)
     d2h = 8 * sw.sw_ncounters(Q_BENCH, sw.SW_POTTS) + 40   # counter row + device state word block
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(sw, torch, dev, args.steps)
+    served = None
+    if not args.no_served and world == 1:
+        served = run_served()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         L_cpu, sweeps_cpu = 4096, 3
@@ -309,6 +373,8 @@ def run_ours(args, world, rank, local):
         "sweep_roofline": sweep_roofline,
         "stage_us": stage_us,
         "update_only_ns_per_flip": update_only,
+        "batched": batched,
+        "served": served,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N, "d2h_bytes_per_step": d2h},
         "gpu_launches": 4 * args.steps,
@@ -325,6 +391,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

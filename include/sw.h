@@ -172,6 +172,15 @@ int sw_get_thresholds(sw_handle *h, uint32_t *out, int n);
 int sw_get_sweep(sw_handle *h, uint64_t *out);
 int sw_set_sweep(sw_handle *h, uint64_t t);
 
+/* Launch shape: resident blocks per SM requested for the four kernels of
+ * a sweep, shape[4] = {labeling, merge, flatten, flip}, each in [1, 64].
+ * Results never depend on it.  sw_autotune times every candidate (n real
+ * sweeps each, they advance the chain like any others), keeps the fastest
+ * per kernel, caches it per (device, work size) for the process, and writes
+ * the choice to shape_out (may be NULL).  A cached choice costs no sweeps. */
+int sw_autotune(sw_handle *h, int n, int *shape_out);
+int sw_set_launch_shape(sw_handle *h, const int *shape);
+
 /* Use a different stream for subsequent work (a cudaStream_t). */
 int sw_set_stream(sw_handle *h, void *stream);
 
@@ -216,8 +225,11 @@ int sw_batch_synchronize(sw_batch *b);
 int sw_batch_set_measure(sw_batch *b, int on);
 int sw_batch_set_graph(sw_batch *b, int on);
 int sw_batch_set_debug_labels(sw_batch *b, int on);
-/* As sw_profile_sweeps, for the batched launch sequence. */
+/* As sw_profile_sweeps / sw_autotune / sw_set_launch_shape, for the batched
+ * launch sequence. */
 int sw_batch_profile_sweeps(sw_batch *b, int n, float *ms, int max_stages);
+int sw_batch_autotune(sw_batch *b, int n, int *shape_out);
+int sw_batch_set_launch_shape(sw_batch *b, const int *shape);
 
 #ifdef __cplusplus
 }

@@ -79,6 +79,8 @@ EXPORTS = [
     ("sw_set_stream", ctypes.c_int, [_H, ctypes.c_void_p]),
     ("sw_set_graph", ctypes.c_int, [_H, ctypes.c_int]),
     ("sw_profile_sweeps", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    ("sw_autotune", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("sw_set_launch_shape", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     ("sw_batch_create", ctypes.c_void_p, [ctypes.c_void_p]),
     ("sw_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("sw_batch_attach", ctypes.c_int, [ctypes.c_void_p, _H]),
@@ -91,6 +93,8 @@ EXPORTS = [
     ("sw_batch_set_debug_labels", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sw_batch_profile_sweeps", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                                ctypes.c_int]),
+    ("sw_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("sw_batch_set_launch_shape", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 ]
 
 
@@ -241,6 +245,28 @@ def sw_profile_sweeps(h, n):
     out = np.zeros(8, dtype=np.float32)
     m = _check(lib().sw_profile_sweeps(h, int(n), _p(out, ctypes.c_float), 8))
     return [float(v) for v in out[:m]]
+
+
+def sw_autotune(h, n=3):
+    out = np.zeros(4, dtype=np.int32)
+    _check(lib().sw_autotune(h, int(n), _p(out, ctypes.c_int)))
+    return [int(v) for v in out]
+
+
+def sw_set_launch_shape(h, shape):
+    a = np.ascontiguousarray(shape, dtype=np.int32)
+    return _check(lib().sw_set_launch_shape(h, _p(a, ctypes.c_int)))
+
+
+def sw_batch_autotune(b, n=3):
+    out = np.zeros(4, dtype=np.int32)
+    _check(lib().sw_batch_autotune(b, int(n), _p(out, ctypes.c_int)))
+    return [int(v) for v in out]
+
+
+def sw_batch_set_launch_shape(b, shape):
+    a = np.ascontiguousarray(shape, dtype=np.int32)
+    return _check(lib().sw_batch_set_launch_shape(b, _p(a, ctypes.c_int)))
 
 
 def sw_batch_create(stream=None):

@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -18,6 +20,7 @@
 
 using swgb::Batch;
 using swgb::DevState;
+using swgb::LaunchShape;
 using swgb::Lattice;
 
 namespace {
@@ -88,6 +91,7 @@ struct sw_handle {
     std::vector<uint32_t> thr_tab;
     int ncounters = 0, nclass = 0;
     bool measure = true, labels = false, record = false, use_graph = false;
+    LaunchShape shape;
     uint64_t t_host = 0;       // sweep index after all enqueued work
     uint64_t t_drained = 0;    // first sweep whose counters are still on the device
     int sticky = SW_OK;
@@ -154,6 +158,7 @@ struct sw_batch {
     bool own_stream = false;
     int sm_count = 0;
     bool measure = true, labels = false, use_graph = false;
+    LaunchShape shape;
     // device descriptor arrays (capacity grows; contents rewritten on change)
     int cap = 0;
     Lattice *d_lat = nullptr;
@@ -302,13 +307,13 @@ int reset_device_index(sw_handle *h, uint64_t t)
 }
 
 // One sweep of batch view b on stream s, from a captured graph when asked.
-int enqueue_sweep(const Batch &b, bool measure, bool labels, int sm_count, cudaStream_t s, bool use_graph,
-                  cudaGraph_t *graph, cudaGraphExec_t *exec)
+int enqueue_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape, cudaStream_t s,
+                  bool use_graph, cudaGraph_t *graph, cudaGraphExec_t *exec)
 {
     if (use_graph) {
         if (!*exec) {
             SW_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            cudaError_t le = swgb::launch_sweep(b, measure, labels, sm_count, s);
+            cudaError_t le = swgb::launch_sweep(b, measure, labels, sm_count, shape, s);
             cudaError_t ce = cudaStreamEndCapture(s, graph);
             if (le != cudaSuccess) return cuda_fail(le, "launch_sweep (capture)");
             if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
@@ -317,15 +322,95 @@ int enqueue_sweep(const Batch &b, bool measure, bool labels, int sm_count, cudaS
         SW_CUDA(cudaGraphLaunch(*exec, s));
         return SW_OK;
     }
-    cudaError_t e = swgb::launch_sweep(b, measure, labels, sm_count, s);
+    cudaError_t e = swgb::launch_sweep(b, measure, labels, sm_count, shape, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch_sweep");
+    return SW_OK;
+}
+
+// n sweeps of view b with CUDA events around every kernel; per-stage mean
+// milliseconds into ms[kMaxStages].  before() runs ahead of every sweep
+// (counter drains), after() once it is enqueued (sweep bookkeeping).
+template <typename Before, typename After>
+int timed_sweeps(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape, cudaStream_t s,
+                 int n, double *ms, Before before, After after)
+{
+    const int nstages = swgb::kMaxStages;
+    cudaEvent_t ev[swgb::kMaxStages + 1];
+    for (int k = 0; k <= nstages; ++k) SW_CUDA(cudaEventCreate(&ev[k]));
+    for (int k = 0; k < nstages; ++k) ms[k] = 0.0;
+    int rc = SW_OK;
+    for (int i = 0; i < n && rc == SW_OK; ++i) {
+        rc = before();
+        if (rc != SW_OK) break;
+        cudaError_t e = swgb::launch_sweep(b, measure, labels, sm_count, shape, s, ev);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "launch_sweep");
+            break;
+        }
+        after();
+        e = cudaEventSynchronize(ev[nstages]);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaEventSynchronize");
+            break;
+        }
+        for (int k = 0; k < nstages; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            ms[k] += t / n;
+        }
+    }
+    for (int k = 0; k <= nstages; ++k) cudaEventDestroy(ev[k]);
+    return rc;
+}
+
+// Launch shapes chosen so far, per device and work size (process-wide).
+std::mutex g_tune_mu;
+std::map<std::string, LaunchShape> g_tune_cache;
+
+std::string tune_key(int nrep, int ntasks, long long nmerge, bool measure)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[384];
+    snprintf(buf, sizeof buf, "%s|%d|%d|%lld|%d", prop.name, nrep, ntasks, nmerge, (int)measure);
+    return buf;
+}
+
+// Coordinate descent over the blocks per SM of each kernel: every
+// candidate runs n timed sweeps (real sweeps of the chain).
+template <typename Timer>
+int autotune_shape(LaunchShape *best, int n, Timer timer)
+{
+    static const int cand_label[] = {4, 6, 8};
+    static const int cand_other[] = {4, 8, 16, 32};
+    double ms[swgb::kMaxStages];
+    for (int stage = 0; stage < swgb::kMaxStages; ++stage) {
+        const int *cand = stage == 0 ? cand_label : cand_other;
+        const int ncand = stage == 0 ? 3 : 4;
+        double best_ms = 1e30;
+        LaunchShape pick = *best;
+        for (int i = 0; i < ncand; ++i) {
+            LaunchShape trial = *best;
+            int *field = stage == 0 ? &trial.label : stage == 1 ? &trial.merge : stage == 2 ? &trial.flatten : &trial.flip;
+            *field = cand[i];
+            int rc = timer(trial, n, ms);
+            if (rc != SW_OK) return rc;
+            if (ms[stage] < best_ms) {
+                best_ms = ms[stage];
+                pick = trial;
+            }
+        }
+        *best = pick;
+    }
     return SW_OK;
 }
 
 int enqueue_one(sw_handle *h)
 {
-    return enqueue_sweep(h->self_batch(), h->measure, h->labels, h->sm_count, h->stream, h->use_graph, &h->graph,
-                         &h->graph_exec);
+    return enqueue_sweep(h->self_batch(), h->measure, h->labels, h->sm_count, h->shape, h->stream, h->use_graph,
+                         &h->graph, &h->graph_exec);
 }
 
 void free_handle(sw_handle *h)
@@ -722,37 +807,79 @@ int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages)
     if (n < 1 || max_stages < 1) return fail(SW_ERR_ARG, "n and max_stages must be positive");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
-    const int nstages = swgb::kMaxStages;
-    cudaEvent_t ev[swgb::kMaxStages + 1];
-    for (int k = 0; k <= nstages; ++k) SW_CUDA(cudaEventCreate(&ev[k]));
-    std::vector<double> acc(nstages, 0.0);
-    for (int s = 0; s < n && rc == SW_OK; ++s) {
-        if (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) rc = drain(h);
-        if (rc != SW_OK) break;
-        cudaError_t e = swgb::launch_sweep(h->self_batch(), h->measure, h->labels, h->sm_count, h->stream, ev);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "launch_sweep");
-            break;
-        }
-        h->t_host++;
-        if (!h->measure) h->t_drained = h->t_host;
-        e = cudaEventSynchronize(ev[nstages]);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "cudaEventSynchronize");
-            break;
-        }
-        for (int k = 0; k < nstages; ++k) {
-            float t = 0.f;
-            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
-            acc[k] += t;
-        }
-    }
-    for (int k = 0; k <= nstages; ++k) cudaEventDestroy(ev[k]);
+    double acc[swgb::kMaxStages];
+    rc = timed_sweeps(
+        h->self_batch(), h->measure, h->labels, h->sm_count, h->shape, h->stream, n, acc,
+        [&]() -> int {
+            return (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) ? drain(h) : (int)SW_OK;
+        },
+        [&]() {
+            h->t_host++;
+            if (!h->measure) h->t_drained = h->t_host;
+        });
     if (rc != SW_OK) return rc;
-    const int m = std::min(nstages, max_stages);
-    for (int k = 0; k < m; ++k) ms[k] = (float)(acc[k] / n);
+    const int m = std::min(swgb::kMaxStages, max_stages);
+    for (int k = 0; k < m; ++k) ms[k] = (float)acc[k];
     rc = drain(h);
     return rc != SW_OK ? rc : m;
+}
+
+int sw_autotune(sw_handle *h, int n, int *shape_out)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (n < 1) return fail(SW_ERR_ARG, "n must be positive");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    const std::string key = tune_key(1, h->ntasks(), h->nmerge(), h->measure);
+    LaunchShape best;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        rc = autotune_shape(&best, n, [&](const LaunchShape &trial, int nn, double *ms) {
+            return timed_sweeps(
+                h->self_batch(), h->measure, h->labels, h->sm_count, trial, h->stream, nn, ms,
+                [&]() -> int {
+                    return (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) ? drain(h)
+                                                                                                       : (int)SW_OK;
+                },
+                [&]() {
+                    h->t_host++;
+                    if (!h->measure) h->t_drained = h->t_host;
+                });
+        });
+        if (rc != SW_OK) return rc;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    h->shape = best;
+    drop_graph(h);
+    if (shape_out) {
+        shape_out[0] = best.label;
+        shape_out[1] = best.merge;
+        shape_out[2] = best.flatten;
+        shape_out[3] = best.flip;
+    }
+    return drain(h);
+}
+
+int sw_set_launch_shape(sw_handle *h, const int *shape)
+{
+    if (!h || !shape) return fail(SW_ERR_ARG, "null argument");
+    for (int k = 0; k < 4; ++k)
+        if (shape[k] < 1 || shape[k] > 64) return fail(SW_ERR_ARG, "blocks per SM must be in [1, 64]");
+    h->shape.label = shape[0];
+    h->shape.merge = shape[1];
+    h->shape.flatten = shape[2];
+    h->shape.flip = shape[3];
+    drop_graph(h);
+    return SW_OK;
 }
 
 int sw_set_graph(sw_handle *h, int on)
@@ -819,6 +946,26 @@ static int rebuild_batch(sw_batch *b)
     }
     b->dirty = false;
     return SW_OK;
+}
+
+static int batch_timed_sweeps(sw_batch *b, const LaunchShape &shape, int n, double *ms)
+{
+    return timed_sweeps(
+        b->view(), b->measure, b->labels, b->sm_count, shape, b->stream, n, ms,
+        [&]() -> int {
+            for (sw_handle *h : b->reps)
+                if (b->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) {
+                    int rc = drain(h);
+                    if (rc != SW_OK) return rc;
+                }
+            return SW_OK;
+        },
+        [&]() {
+            for (sw_handle *h : b->reps) {
+                h->t_host++;
+                if (!b->measure) h->t_drained = h->t_host;
+            }
+        });
 }
 
 sw_batch *sw_batch_create(void *stream)
@@ -927,8 +1074,8 @@ int sw_batch_sweep(sw_batch *b, int n)
                 if (rc != SW_OK) return rc;
             }
         }
-        int rc = enqueue_sweep(b->view(), b->measure, b->labels, b->sm_count, b->stream, b->use_graph, &b->graph,
-                               &b->graph_exec);
+        int rc = enqueue_sweep(b->view(), b->measure, b->labels, b->sm_count, b->shape, b->stream, b->use_graph,
+                               &b->graph, &b->graph_exec);
         if (rc != SW_OK) return rc;
         for (sw_handle *h : b->reps) {
             h->t_host++;
@@ -988,40 +1135,64 @@ int sw_batch_profile_sweeps(sw_batch *b, int n, float *ms, int max_stages)
         int rc = rebuild_batch(b);
         if (rc != SW_OK) return rc;
     }
-    const int nstages = swgb::kMaxStages;
-    cudaEvent_t ev[swgb::kMaxStages + 1];
-    for (int k = 0; k <= nstages; ++k) SW_CUDA(cudaEventCreate(&ev[k]));
-    std::vector<double> acc(nstages, 0.0);
-    int rc = SW_OK;
-    for (int s = 0; s < n && rc == SW_OK; ++s) {
-        for (sw_handle *h : b->reps)
-            if (rc == SW_OK && b->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) rc = drain(h);
-        if (rc != SW_OK) break;
-        cudaError_t e = swgb::launch_sweep(b->view(), b->measure, b->labels, b->sm_count, b->stream, ev);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "launch_sweep");
-            break;
-        }
-        for (sw_handle *h : b->reps) {
-            h->t_host++;
-            if (!b->measure) h->t_drained = h->t_host;
-        }
-        e = cudaEventSynchronize(ev[nstages]);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "cudaEventSynchronize");
-            break;
-        }
-        for (int k = 0; k < nstages; ++k) {
-            float t = 0.f;
-            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
-            acc[k] += t;
+    double acc[swgb::kMaxStages];
+    int rc = batch_timed_sweeps(b, b->shape, n, acc);
+    if (rc != SW_OK) return rc;
+    const int m = std::min(swgb::kMaxStages, max_stages);
+    for (int k = 0; k < m; ++k) ms[k] = (float)acc[k];
+    return m;
+}
+
+int sw_batch_autotune(sw_batch *b, int n, int *shape_out)
+{
+    if (!b) return fail(SW_ERR_ARG, "null batch");
+    if (n < 1) return fail(SW_ERR_ARG, "n must be positive");
+    if (b->reps.empty()) return fail(SW_ERR_STATE, "empty batch");
+    if (b->dirty) {
+        int rc = rebuild_batch(b);
+        if (rc != SW_OK) return rc;
+    }
+    const std::string key = tune_key((int)b->reps.size(), b->ntasks, b->nmerge, b->measure);
+    LaunchShape best;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
         }
     }
-    for (int k = 0; k <= nstages; ++k) cudaEventDestroy(ev[k]);
-    if (rc != SW_OK) return rc;
-    const int m = std::min(nstages, max_stages);
-    for (int k = 0; k < m; ++k) ms[k] = (float)(acc[k] / n);
-    return m;
+    if (!cached) {
+        int rc = autotune_shape(&best, n, [&](const LaunchShape &trial, int nn, double *ms) {
+            return batch_timed_sweeps(b, trial, nn, ms);
+        });
+        if (rc != SW_OK) return rc;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    b->shape = best;
+    drop_batch_graph(b);
+    if (shape_out) {
+        shape_out[0] = best.label;
+        shape_out[1] = best.merge;
+        shape_out[2] = best.flatten;
+        shape_out[3] = best.flip;
+    }
+    return sw_batch_synchronize(b);
+}
+
+int sw_batch_set_launch_shape(sw_batch *b, const int *shape)
+{
+    if (!b || !shape) return fail(SW_ERR_ARG, "null argument");
+    for (int k = 0; k < 4; ++k)
+        if (shape[k] < 1 || shape[k] > 64) return fail(SW_ERR_ARG, "blocks per SM must be in [1, 64]");
+    b->shape.label = shape[0];
+    b->shape.merge = shape[1];
+    b->shape.flatten = shape[2];
+    b->shape.flip = shape[3];
+    drop_batch_graph(b);
+    return SW_OK;
 }
 
 }  // extern "C"

@@ -39,10 +39,16 @@ cudaError_t launch_init(const Lattice &lat, int random, int sm_count, cudaStream
 cudaError_t launch_pending_classes(const Lattice &lat, int sm_count, cudaStream_t s);
 // Number of spins outside [0, q) is added to *bad (device word).
 cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_count, cudaStream_t s);
+// Launch shape of a sweep: resident blocks per SM requested for each of
+// the four kernels (the grids never exceed the work).  Any shape gives the
+// same results; only the speed differs.
+struct LaunchShape {
+    int label = 8, merge = 16, flatten = 16, flip = 16;
+};
 // ev (optional): events recorded before the first and after every kernel of
 // the sweep (kMaxStages + 1 entries).
 constexpr int kMaxStages = 4;
-cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, cudaStream_t s,
-                         cudaEvent_t *ev = nullptr);
+cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape,
+                         cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 }  // namespace swgb

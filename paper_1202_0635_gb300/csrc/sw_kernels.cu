@@ -821,24 +821,23 @@ __global__ void k_count_invalid(const int8_t *spin, long long n, int q, unsigned
 }
 
 template <bool MEASURE, bool LABELS>
-cudaError_t sweep_impl(const Batch &b, int sm_count, cudaStream_t s, cudaEvent_t *ev)
+cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, cudaStream_t s, cudaEvent_t *ev)
 {
     int nev = 0;
     auto mark = [&]() {
         if (ev) cudaEventRecord(ev[nev++], s);
     };
-    const int blocks = std::max(1, std::min(b.ntasks, sm_count * 8));
+    const int blocks = std::max(1, std::min(b.ntasks, sm_count * shape.label));
     mark();
     k_label_tiles<MEASURE, LABELS><<<blocks, kBlockThreads, 0, s>>>(b);
     mark();
     const int mblocks =
-        (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * 16));
+        (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * shape.merge));
     k_merge<<<mblocks, 256, 0, s>>>(b);
     mark();
-    const int fblocks = std::max(1, std::min(b.ntasks, sm_count * 16));
-    k_flatten<MEASURE><<<fblocks, kBlockThreads, 0, s>>>(b);
+    k_flatten<MEASURE><<<std::max(1, std::min(b.ntasks, sm_count * shape.flatten)), kBlockThreads, 0, s>>>(b);
     mark();
-    k_flip_tiles<MEASURE, LABELS><<<fblocks, kBlockThreads, 0, s>>>(b);
+    k_flip_tiles<MEASURE, LABELS><<<std::max(1, std::min(b.ntasks, sm_count * shape.flip)), kBlockThreads, 0, s>>>(b);
     mark();
     return cudaGetLastError();
 }
@@ -874,12 +873,14 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, cudaStream_t s,
-                         cudaEvent_t *ev)
+cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape,
+                         cudaStream_t s, cudaEvent_t *ev)
 {
     if (measure)
-        return labels ? sweep_impl<true, true>(b, sm_count, s, ev) : sweep_impl<true, false>(b, sm_count, s, ev);
-    return labels ? sweep_impl<false, true>(b, sm_count, s, ev) : sweep_impl<false, false>(b, sm_count, s, ev);
+        return labels ? sweep_impl<true, true>(b, sm_count, shape, s, ev)
+                      : sweep_impl<true, false>(b, sm_count, shape, s, ev);
+    return labels ? sweep_impl<false, true>(b, sm_count, shape, s, ev)
+                  : sweep_impl<false, false>(b, sm_count, shape, s, ev);
 }
 
 }  // namespace swgb

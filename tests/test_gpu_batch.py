@@ -104,3 +104,42 @@ def test_batch_measure_off_and_labels():
         assert np.array_equal(lat.spins, ref.spins)
         assert lat.measure().nmeas == 2
     b.close()
+
+
+def test_launch_shapes_never_change_results():
+    Tc = 1.0 / math.log(1.0 + math.sqrt(2.0))
+    ref = None
+    for shape in ([8, 16, 16, 16], [1, 1, 1, 1], [4, 32, 8, 4], [6, 3, 64, 2]):
+        lat = sw.Lattice(200, 2, sw.SW_POTTS, Tc, 9, init=sw.SW_INIT_RANDOM)
+        sw.sw_set_launch_shape(lat.h, shape)
+        sw.sw_set_record(lat.h, 1)
+        lat.sweep(10)
+        got = (lat.spins.copy(), lat.take_counts())
+        lat.close()
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), shape
+
+
+def test_autotune_picks_a_cached_shape_and_keeps_the_chain():
+    Tc = 1.0 / math.log(1.0 + math.sqrt(3.0))
+    lat = sw.Lattice(256, 3, sw.SW_POTTS, Tc, 4, init=sw.SW_INIT_RANDOM)
+    shape = sw.sw_autotune(lat.h, 2)
+    assert all(1 <= v <= 64 for v in shape)
+    t = lat.sweep_index
+    assert t == 2 * (3 + 4 + 4 + 4)          # every candidate ran real sweeps
+    o = Oracle(256, 3, POTTS, Tc, 4, init="random")
+    o.sweep(t)
+    assert np.array_equal(lat.spins, o.spins)
+    again = sw.Lattice(256, 3, sw.SW_POTTS, Tc, 5, init=sw.SW_INIT_RANDOM)
+    assert sw.sw_autotune(again.h, 2) == shape   # cached: no sweeps
+    assert again.sweep_index == 0
+    lat.close()
+    again.close()
+    b = sw.Batch()
+    for L in (32, 96, 160):
+        b.add(L, 2, sw.SW_POTTS, 1.0 / math.log(1.0 + math.sqrt(2.0)), L, init=sw.SW_INIT_RANDOM)
+    bshape = sw.sw_batch_autotune(b.b, 1)
+    assert all(1 <= v <= 64 for v in bshape)
+    b.close()
