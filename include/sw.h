@@ -231,6 +231,50 @@ int sw_batch_profile_sweeps(sw_batch *b, int n, float *ms, int max_stages);
 int sw_batch_autotune(sw_batch *b, int n, int *shape_out);
 int sw_batch_set_launch_shape(sw_batch *b, const int *shape);
 
+/* ------------------------------------------------------------------------
+ * Sweeps without device allocation.  The paper has no counterpart: this is
+ * a convenience of the library's interface.
+ *
+ * Some callers cannot allocate device memory at the point where they want
+ * to sweep: a plugin running inside a host framework that hands out all
+ * device memory from its own pool (an allocation of its own would fail once
+ * the pool holds the memory, or escape the host's accounting), or a
+ * latency-bound loop where cudaMalloc / cudaFree could stall on an implicit
+ * device synchronisation.  sw_sweep_noalloc serves them: it takes the
+ * spins (and, optionally, a counter buffer) from the caller and keeps all
+ * its working memory in one fixed array of SW_NOALLOC_SCRATCH_BYTES bytes
+ * compiled into the library, which every device that loads the library
+ * holds until the process exits.  It calls no allocating routine.
+ *
+ * It runs n sweeps with the kernels and random streams of sw_sweep: the
+ * result equals that of a handle made by sw_create(L, q, model, T, seed)
+ * holding the same spins at sweep index sweep0, after sw_sweep(h, n).
+ *   d_spins   device, L*L int8 states in [0, q), row-major, 16-byte aligned;
+ *             read and overwritten in place.  If any state lies outside
+ *             [0, q) the call returns SW_ERR_ARG and changes nothing.
+ *   d_counts  device, n * sw_ncounters(q, model) int64, 8-byte aligned, or
+ *             NULL: row k receives the counters of sweep sweep0 + k (the
+ *             rows sw_take_counts would return).  NULL skips measurement.
+ *   sweep0    sweeps completed before this call (positions the random
+ *             stream); a chain continues with sweep0 + n on the next call.
+ *   stream    cudaStream_t for all work (NULL = legacy default stream).
+ * Limits: 4 <= L <= SW_NOALLOC_MAX_L with L % 4 == 0, and the q / model / T
+ * rules of sw_create; anything else returns SW_ERR_ARG before any GPU work.
+ * The call returns once its work on `stream` is complete.
+ *
+ * The first call on a device looks up the array's device address (and may
+ * load the library's device code onto that device); make that first call
+ * before any stream capture begins.  All calls on a device share the array,
+ * which keeps the previous call's contents (each call resets what must
+ * start from a known value): calls whose work overlaps on the GPU, from
+ * several threads or streams, race and corrupt each other's results, so
+ * serialise them.
+ * ---------------------------------------------------------------------- */
+#define SW_NOALLOC_MAX_L 1024
+#define SW_NOALLOC_SCRATCH_BYTES (7 * 1024 * 1024)
+int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed, uint64_t sweep0, int n,
+                     int8_t *d_spins, int64_t *d_counts, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

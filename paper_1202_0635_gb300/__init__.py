@@ -21,6 +21,8 @@ SW_INIT_UP, SW_INIT_RANDOM = 0, 1
 SW_MAX_Q = 127
 SW_MAX_CLOCK_Q = 64
 SW_MAX_COUNTERS = SW_MAX_Q + SW_MAX_Q // 2 + 1 + 2
+SW_NOALLOC_MAX_L = 1024
+SW_NOALLOC_SCRATCH_BYTES = 7 * 1024 * 1024
 
 
 class SwError(RuntimeError):
@@ -95,6 +97,9 @@ EXPORTS = [
                                                ctypes.c_int]),
     ("sw_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("sw_batch_set_launch_shape", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("sw_sweep_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                        ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
 ]
 
 
@@ -316,6 +321,14 @@ def sw_batch_profile_sweeps(b, n):
     out = np.zeros(8, dtype=np.float32)
     m = _check(lib().sw_batch_profile_sweeps(b, int(n), _p(out, ctypes.c_float), 8))
     return [float(v) for v in out[:m]]
+
+
+def sw_sweep_noalloc(L, q, model, T, seed, sweep0, n, d_spins, d_counts=None, stream=None):
+    """n sweeps of caller-owned device spins (address d_spins) starting at
+    sweep index sweep0, with no device allocation; d_counts (device address
+    of n x sw_ncounters int64, or None) receives the per-sweep counters."""
+    return _check(lib().sw_sweep_noalloc(int(L), int(q), int(model), float(T), ctypes.c_uint64(int(seed)),
+                                         ctypes.c_uint64(int(sweep0)), int(n), d_spins, d_counts, stream))
 
 
 class Lattice:

@@ -1196,3 +1196,217 @@ int sw_batch_set_launch_shape(sw_batch *b, const int *shape)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// sw_sweep_noalloc: sweeps of a caller-owned spin array with every piece of
+// working memory taken from one fixed device array of this file, so that the
+// call allocates nothing.  It runs the same four kernels as sw_sweep, on a
+// batch-of-one view whose buffers are carved out of that array.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Byte offsets of the working buffers inside the shared array, sized for
+// the largest accepted lattice (SW_NOALLOC_MAX_L).
+struct NoallocLayout {
+    size_t label, code, open_list, open_state, open_count, cross, ring, thr_tab, st, lat, task_off, merge_off,
+        ticket, total;
+};
+constexpr int kNoallocRingSlots = 256;   // counter rows; longer calls are drained in chunks
+
+constexpr NoallocLayout noalloc_layout()
+{
+    const size_t sites = (size_t)SW_NOALLOC_MAX_L * SW_NOALLOC_MAX_L;
+    const size_t tiles = (size_t)((SW_NOALLOC_MAX_L + swgb::kTileW - 1) / swgb::kTileW) *
+                         ((SW_NOALLOC_MAX_L + swgb::kTileH - 1) / swgb::kTileH);
+    NoallocLayout o{};
+    size_t at = 0;
+    o.label = at;      at = align256(at + sites * sizeof(int32_t));
+    o.code = at;       at = align256(at + sites * sizeof(uint16_t));
+    o.open_list = at;  at = align256(at + tiles * swgb::kOpenSlots * sizeof(int32_t));
+    o.open_state = at; at = align256(at + tiles * swgb::kOpenSlots);
+    o.open_count = at; at = align256(at + tiles * sizeof(int32_t));
+    o.cross = at;      at = align256(at + tiles * swgb::kCrossWords * sizeof(uint32_t));
+    o.ring = at;       at = align256(at + (size_t)kNoallocRingSlots * SW_MAX_COUNTERS * sizeof(unsigned long long));
+    o.thr_tab = at;    at = align256(at + (size_t)(2 * SW_MAX_CLOCK_Q) * (2 * SW_MAX_CLOCK_Q) * sizeof(uint32_t));
+    o.st = at;         at = align256(at + sizeof(DevState));
+    o.lat = at;        at = align256(at + sizeof(Lattice));
+    o.task_off = at;   at = align256(at + 2 * sizeof(int));
+    o.merge_off = at;  at = align256(at + 2 * sizeof(long long));
+    o.ticket = at;     at = align256(at + sizeof(unsigned int));
+    o.total = at;
+    return o;
+}
+constexpr NoallocLayout kNoalloc = noalloc_layout();
+static_assert(kNoalloc.total <= SW_NOALLOC_SCRATCH_BYTES, "SW_NOALLOC_SCRATCH_BYTES is too small for the layout");
+
+}  // namespace
+
+// The working memory of sw_sweep_noalloc.  Each device that loads the
+// library holds one copy until the process exits.  Host code must not take
+// its address directly (the name is a host-side stand-in); the per-device
+// address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SW_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_base[kNoallocMaxDevices];   // device address of the array, per device
+int g_noalloc_sms[kNoallocMaxDevices];
+
+// Once per device, with that device current: the array's device address
+// and the SM count.  The first lookup may load the library's device code
+// onto the device.
+int noalloc_setup(int dev, unsigned char **base, int *sms)
+{
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(SW_ERR_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        g_noalloc_sms[dev] = n;
+        g_noalloc_base[dev] = (unsigned char *)p;
+    }
+    *base = g_noalloc_base[dev];
+    *sms = g_noalloc_sms[dev];
+    return SW_OK;
+}
+
+}  // namespace
+
+extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed, uint64_t sweep0, int n,
+                                int8_t *d_spins, int64_t *d_counts, void *stream)
+{
+    if (validate(L, q, model, T) != SW_OK) return SW_ERR_ARG;
+    if (L > SW_NOALLOC_MAX_L)
+        return fail(SW_ERR_ARG, "L=%d exceeds the no-allocation limit L <= %d (%d bytes of scratch per device)", L,
+                    SW_NOALLOC_MAX_L, SW_NOALLOC_SCRATCH_BYTES);
+    if (n < 0) return fail(SW_ERR_ARG, "n=%d < 0", n);
+    if (!d_spins || ((uintptr_t)d_spins & 15)) return fail(SW_ERR_ARG, "spins must be a 16-byte aligned device buffer");
+    if (d_counts && ((uintptr_t)d_counts & 7)) return fail(SW_ERR_ARG, "counts must be 8-byte aligned");
+    if (n == 0) return SW_OK;
+
+    int dev = 0, sms = 0;
+    unsigned char *base = nullptr;
+    SW_CUDA(cudaGetDevice(&dev));
+    int rc = noalloc_setup(dev, &base, &sms);
+    if (rc != SW_OK) return rc;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const bool measure = d_counts != nullptr;
+    const int nclass = nclass_of(q, model), nc = q + nclass + 2;
+    const int tiles_x = (L + swgb::kTileW - 1) / swgb::kTileW, tiles_y = (L + swgb::kTileH - 1) / swgb::kTileH;
+
+    Lattice lat{};
+    lat.L = L;
+    lat.q = q;
+    lat.clock = model == SW_CLOCK;
+    lat.key0 = (uint32_t)(seed & 0xffffffffu);
+    lat.key1 = (uint32_t)(seed >> 32);
+    lat.spin = d_spins;
+    lat.label = (int32_t *)(base + kNoalloc.label);
+    lat.code = (uint16_t *)(base + kNoalloc.code);
+    lat.open_list = (int32_t *)(base + kNoalloc.open_list);
+    lat.open_state = base + kNoalloc.open_state;
+    lat.open_count = (int32_t *)(base + kNoalloc.open_count);
+    lat.cross = (uint32_t *)(base + kNoalloc.cross);
+    lat.tiles_x = tiles_x;
+    lat.tiles_y = tiles_y;
+    lat.st = (DevState *)(base + kNoalloc.st);
+    lat.ring = (unsigned long long *)(base + kNoalloc.ring);
+    lat.ring_slots = kNoallocRingSlots;
+    lat.ncounters = nc;
+    lat.nclass = nclass;
+    // Bond thresholds (Sec. 2 step (ii); clock: Sec. 4 embedding), J = 1,
+    // built exactly as sw_create builds them.
+    std::vector<uint32_t> tab;
+    if (model == SW_POTTS) {
+        lat.thr = threshold_of(1.0 / T);
+    } else if (model == SW_ISING) {
+        lat.thr = threshold_of(2.0 / T);
+    } else {
+        const int n2 = 2 * q;
+        tab.assign((size_t)n2 * n2, 0u);
+        for (int a = 0; a < n2; ++a) {
+            for (int b = 0; b < n2; ++b) {
+                const int side_a = (a % q == 0) ? 0 : (a < q ? 1 : -1);
+                const int side_b = (b % q == 0) ? 0 : (b < q ? 1 : -1);
+                if (side_a == 0 || side_a != side_b) continue;
+                const double pa = std::sin((M_PI * (double)(a % q)) / (double)q);
+                const double pb = std::sin((M_PI * (double)(b % q)) / (double)q);
+                tab[(size_t)a * n2 + b] = threshold_of((2.0 / T) * (pa * pb));
+            }
+        }
+        lat.thr_tab = (const uint32_t *)(base + kNoalloc.thr_tab);
+    }
+    const int task_off[2] = {0, tiles_x * tiles_y};
+    const long long merge_off[2] = {0, (long long)L * (tiles_x + tiles_y)};
+    Batch b{};
+    b.lat = (const Lattice *)(base + kNoalloc.lat);
+    b.task_off = (const int *)(base + kNoalloc.task_off);
+    b.merge_off = (const long long *)(base + kNoalloc.merge_off);
+    b.ticket = (unsigned int *)(base + kNoalloc.ticket);
+    b.nrep = 1;
+    b.ntasks = task_off[1];
+    b.nmerge = merge_off[1];
+
+    // The array keeps whatever the previous call left: reset everything that
+    // must start from a known value (sweep index, error word, ticket,
+    // counter rows).  Labels, codes and open lists are written before read.
+    DevState st{};
+    st.sweep = sweep0;
+    st.classes_upto = sweep0;
+    SW_CUDA(cudaMemcpyAsync(lat.st, &st, sizeof st, cudaMemcpyHostToDevice, s));
+    SW_CUDA(cudaMemsetAsync(b.ticket, 0, sizeof(unsigned int), s));
+    SW_CUDA(cudaMemsetAsync(lat.ring, 0, sizeof(unsigned long long) * kNoallocRingSlots * nc, s));
+    SW_CUDA(cudaMemcpyAsync(base + kNoalloc.lat, &lat, sizeof lat, cudaMemcpyHostToDevice, s));
+    SW_CUDA(cudaMemcpyAsync(base + kNoalloc.task_off, task_off, sizeof task_off, cudaMemcpyHostToDevice, s));
+    SW_CUDA(cudaMemcpyAsync(base + kNoalloc.merge_off, merge_off, sizeof merge_off, cudaMemcpyHostToDevice, s));
+    if (!tab.empty())
+        SW_CUDA(cudaMemcpyAsync(base + kNoalloc.thr_tab, tab.data(), tab.size() * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, s));
+
+    // Every kernel assumes states in [0, q): check them first, change nothing otherwise.
+    cudaError_t e = swgb::launch_count_invalid(lat, &lat.st->scratch, sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_count_invalid");
+    unsigned int nbad = 0;
+    SW_CUDA(cudaMemcpyAsync(&nbad, &lat.st->scratch, sizeof nbad, cudaMemcpyDeviceToHost, s));
+    SW_CUDA(cudaStreamSynchronize(s));
+    if (nbad) return fail(SW_ERR_ARG, "%u spins outside [0, %d); nothing was changed", nbad, q);
+
+    // Sweeps in chunks that fit the counter rows; after each chunk the
+    // newest configuration's bond classes are completed and the chunk's rows
+    // copied to d_counts (row k = sweep sweep0 + k).
+    const LaunchShape shape;
+    for (int done = 0; done < n;) {
+        const int c = std::min(n - done, kNoallocRingSlots - 1);
+        for (int k = 0; k < c; ++k) {
+            e = swgb::launch_sweep(b, measure, false, sms, shape, s);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_sweep");
+        }
+        if (measure) {
+            e = swgb::launch_pending_classes(lat, sms, s);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_pending_classes");
+            const uint64_t t0 = sweep0 + (uint64_t)done;
+            const size_t first = (size_t)(t0 % kNoallocRingSlots);
+            const size_t n1 = std::min((size_t)c, (size_t)kNoallocRingSlots - first);
+            const size_t row = (size_t)nc * sizeof(unsigned long long);
+            SW_CUDA(cudaMemcpyAsync(d_counts + (size_t)done * nc, lat.ring + first * nc, n1 * row,
+                                    cudaMemcpyDeviceToDevice, s));
+            if (n1 < (size_t)c)
+                SW_CUDA(cudaMemcpyAsync(d_counts + ((size_t)done + n1) * nc, lat.ring, ((size_t)c - n1) * row,
+                                        cudaMemcpyDeviceToDevice, s));
+        }
+        done += c;
+    }
+    SW_CUDA(cudaMemcpyAsync(&st, lat.st, sizeof st, cudaMemcpyDeviceToHost, s));
+    SW_CUDA(cudaStreamSynchronize(s));
+    if (st.err != swgb::kErrNone)
+        return fail(SW_ERR_NOT_CONVERGED, "device loop bound exceeded (code %d at index %d)", st.err, st.err_where);
+    return SW_OK;
+}
