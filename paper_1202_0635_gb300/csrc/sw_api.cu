@@ -78,6 +78,7 @@ struct sw_handle {
     int32_t *d_open_list = nullptr, *d_open_count = nullptr;
     uint8_t *d_open_state = nullptr;
     uint32_t *d_cross = nullptr;
+    uint32_t *d_bond = nullptr;
     int tiles_x = 0, tiles_y = 0;
     DevState *d_st = nullptr;
     unsigned long long *d_ring = nullptr;
@@ -122,6 +123,7 @@ struct sw_handle {
         lat.open_count = d_open_count;
         lat.open_state = d_open_state;
         lat.cross = d_cross;
+        lat.bond = d_bond;
         lat.tiles_x = tiles_x;
         lat.tiles_y = tiles_y;
         lat.st = d_st;
@@ -386,19 +388,21 @@ int autotune_shape(LaunchShape *best, int n, Timer timer)
     static const int cand_label[] = {4, 6, 8};
     static const int cand_other[] = {4, 8, 16, 32};
     double ms[swgb::kMaxStages];
-    for (int stage = 0; stage < swgb::kMaxStages; ++stage) {
-        const int *cand = stage == 0 ? cand_label : cand_other;
-        const int ncand = stage == 0 ? 3 : 4;
+    // Timed stages 1..4 are the labeling, merge, flatten and flip kernels
+    // (stage 0, the bond kernel, has a fixed shape).
+    for (int k = 0; k < 4; ++k) {
+        const int *cand = k == 0 ? cand_label : cand_other;
+        const int ncand = k == 0 ? 3 : 4;
         double best_ms = 1e30;
         LaunchShape pick = *best;
         for (int i = 0; i < ncand; ++i) {
             LaunchShape trial = *best;
-            int *field = stage == 0 ? &trial.label : stage == 1 ? &trial.merge : stage == 2 ? &trial.flatten : &trial.flip;
+            int *field = k == 0 ? &trial.label : k == 1 ? &trial.merge : k == 2 ? &trial.flatten : &trial.flip;
             *field = cand[i];
             int rc = timer(trial, n, ms);
             if (rc != SW_OK) return rc;
-            if (ms[stage] < best_ms) {
-                best_ms = ms[stage];
+            if (ms[k + 1] < best_ms) {
+                best_ms = ms[k + 1];
                 pick = trial;
             }
         }
@@ -426,6 +430,7 @@ void free_handle(sw_handle *h)
     if (h->d_open_count) cudaFree(h->d_open_count);
     if (h->d_open_state) cudaFree(h->d_open_state);
     if (h->d_cross) cudaFree(h->d_cross);
+    if (h->d_bond) cudaFree(h->d_bond);
     if (h->d_st) cudaFree(h->d_st);
     if (h->d_ring) cudaFree(h->d_ring);
     if (h->d_self) cudaFree(h->d_self);
@@ -511,6 +516,8 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
         return bail(e, "cudaMalloc(open states)");
     if ((e = cudaMalloc(&h->d_cross, ntiles * swgb::kCrossWords * sizeof(uint32_t))) != cudaSuccess)
         return bail(e, "cudaMalloc(crossing bonds)");
+    if ((e = cudaMalloc(&h->d_bond, ntiles * swgb::kBondWords * sizeof(uint32_t))) != cudaSuccess)
+        return bail(e, "cudaMalloc(bond masks)");
     if ((e = cudaMalloc(&h->d_ring, sizeof(unsigned long long) * swgb::kRingSlots * h->ncounters)) != cudaSuccess)
         return bail(e, "cudaMalloc(ring)");
 
@@ -1210,10 +1217,10 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the working buffers inside the shared array, sized for
 // the largest accepted lattice (SW_NOALLOC_MAX_L).
 struct NoallocLayout {
-    size_t label, code, open_list, open_state, open_count, cross, ring, thr_tab, st, lat, task_off, merge_off,
-        ticket, total;
+    size_t label, code, open_list, open_state, open_count, cross, bond, ring, thr_tab, st, lat, task_off,
+        merge_off, ticket, total;
 };
-constexpr int kNoallocRingSlots = 256;   // counter rows; longer calls are drained in chunks
+constexpr int kNoallocRingSlots = 128;   // counter rows; longer calls are drained in chunks
 
 constexpr NoallocLayout noalloc_layout()
 {
@@ -1228,6 +1235,7 @@ constexpr NoallocLayout noalloc_layout()
     o.open_state = at; at = align256(at + tiles * swgb::kOpenSlots);
     o.open_count = at; at = align256(at + tiles * sizeof(int32_t));
     o.cross = at;      at = align256(at + tiles * swgb::kCrossWords * sizeof(uint32_t));
+    o.bond = at;       at = align256(at + tiles * swgb::kBondWords * sizeof(uint32_t));
     o.ring = at;       at = align256(at + (size_t)kNoallocRingSlots * SW_MAX_COUNTERS * sizeof(unsigned long long));
     o.thr_tab = at;    at = align256(at + (size_t)(2 * SW_MAX_CLOCK_Q) * (2 * SW_MAX_CLOCK_Q) * sizeof(uint32_t));
     o.st = at;         at = align256(at + sizeof(DevState));
@@ -1315,6 +1323,7 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     lat.open_state = base + kNoalloc.open_state;
     lat.open_count = (int32_t *)(base + kNoalloc.open_count);
     lat.cross = (uint32_t *)(base + kNoalloc.cross);
+    lat.bond = (uint32_t *)(base + kNoalloc.bond);
     lat.tiles_x = tiles_x;
     lat.tiles_y = tiles_y;
     lat.st = (DevState *)(base + kNoalloc.st);

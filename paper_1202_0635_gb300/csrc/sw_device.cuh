@@ -45,6 +45,8 @@ struct Lattice {
     uint8_t *open_state;        // tiles x kOpenSlots new state / reflect flag of each open root's cluster
     int32_t *open_count;        // tiles
     uint32_t *cross;            // tiles x 2 words: active crossing bonds (right edge rows, bottom edge columns)
+    uint32_t *bond;             // tiles x 256 words: a tile's right-bond masks (64 rows x 2 words), then
+                                // its down-bond masks; bit c of word (row, h) = bond of column 32 h + c
     int tiles_x, tiles_y;
     DevState *st;
     unsigned long long *ring;   // ring_slots x ncounters counters
@@ -186,32 +188,70 @@ __device__ __forceinline__ int valid_state(int s, int q)
     return (unsigned)s < (unsigned)q ? s : 0;
 }
 
-// Shared-memory union-find on tile-local indices (same invariants).
-__device__ __forceinline__ int find_s(volatile int *par, int x, int cap)
+// Shared-memory union-find over the nodes v = row * 64 + column of a tile
+// (same invariants), one 16-bit parent word per node.  Node v lives in slot
+// v ^ (row & 31): the same column of different rows falls in different
+// banks.  The map is its own inverse.  Parent words below kTileResolved
+// are nodes; a word >= kTileResolved marks a root whose cluster is settled
+// (it carries the cluster's code).
+constexpr int kTileResolved = 0x1000;
+
+__device__ __forceinline__ int tile_slot(int v)
+{
+    return v ^ ((v >> 6) & 31);
+}
+
+__device__ __forceinline__ int par_ld(const volatile uint16_t *par, int v)
+{
+    return par[tile_slot(v)];
+}
+
+// Root of x with path halving (writes only ancestors).  Valid while no word
+// is resolved.  Returns -1 if the cap is exceeded.
+__device__ __forceinline__ int find_t(volatile uint16_t *par, int x, int cap)
 {
     for (int it = 0; it < cap; ++it) {
-        const int p = par[x];
+        const int p = par_ld(par, x);
         if (p == x) return x;
-        const int gp = par[p];
+        const int gp = par_ld(par, p);
         if (gp == p) return p;
-        par[x] = gp;
+        par[tile_slot(x)] = (uint16_t)gp;
         x = gp;
     }
     return -1;
 }
 
-__device__ __forceinline__ bool union_s(volatile int *par, int a, int b, int cap)
+// Link root hi under lo if hi is still a root; returns hi's parent word as
+// it was (== hi on success).  A compare-and-swap on the 32-bit word that
+// holds the 16-bit slot.
+__device__ __forceinline__ int link_t(volatile uint16_t *par, int hi, int lo)
+{
+    const int s = tile_slot(hi);
+    unsigned int *w = (unsigned int *)(par) + (s >> 1);
+    const int sh = 16 * (s & 1);
+    unsigned int old = *(volatile unsigned int *)w;
+    for (;;) {
+        const int cur = (int)((old >> sh) & 0xFFFFu);
+        if (cur != hi) return cur;
+        const unsigned int nw = (old & ~(0xFFFFu << sh)) | ((unsigned int)lo << sh);
+        const unsigned int seen = atomicCAS(w, old, nw);
+        if (seen == old) return hi;
+        old = seen;
+    }
+}
+
+__device__ __forceinline__ bool union_t(volatile uint16_t *par, int a, int b, int cap)
 {
     for (int it = 0; it < cap; ++it) {
-        a = find_s(par, a, cap);
-        b = find_s(par, b, cap);
+        a = find_t(par, a, cap);
+        b = find_t(par, b, cap);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
         const int hi = a > b ? a : b;
         const int lo = a > b ? b : a;
-        const int old = atomicMin((int *)&par[hi], lo);
+        const int old = link_t(par, hi, lo);
         if (old == hi) return true;
-        a = old;
+        a = old;   // hi was linked meanwhile: join its new parent and lo
         b = lo;
     }
     return false;

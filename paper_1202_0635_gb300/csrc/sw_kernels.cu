@@ -1,24 +1,26 @@
 // sw_kernels.cu -- the kernels of one Swendsen-Wang sweep on sm_103a.
 //
 // One sweep (Komura & Okabe, arXiv:1202.0635, Sec. 2 steps (i)-(viii);
-// clock model: Sec. 4 embedded clusters) is four launches over the 64 x 64
+// clock model: Sec. 4 embedded clusters) is five launches over the 64 x 64
 // tiles of every lattice of a batch (a single lattice is a batch of one).
-// A block owns one tile of one lattice at a time ("task"); each of its four
-// warps owns a 32 x 32 quadrant, so per-lattice counters reduce per block.
+// A block owns one tile of one lattice at a time ("task"), so per-lattice
+// counters reduce per block.
 //
-//   k_label_tiles  bonds of every site (Sec. 2 (ii)): equal-neighbour masks
+//   k_bonds        bonds of every site (Sec. 2 (ii)): equal-neighbour masks
 //                  from packed byte compares, Philox draws against the
-//                  integer threshold.  Tile-local clusters by a scanline over
-//                  the rows with a union-find in shared memory.  A component
-//                  that does not reach the tile border (or reaches it only
-//                  through inactive crossing bonds on the right/bottom
-//                  edges) is a finished cluster: its root (smallest site)
-//                  draws the new state here (Sec. 2 (v)-(vii) / Sec. 4
-//                  reflection) and its sites get a "closed" code.  Open
+//                  integer threshold; the masks go to a per-tile buffer.
+//                  With measurement on it also counts the bond classes of
+//                  the incoming configuration (the previous sweep's result)
+//                  and the active bonds.
+//   k_label_tiles  tile-local clusters by a row-by-row labeling with a
+//                  union-find in shared memory (four warps, one 32 x 32
+//                  quadrant each).  A component that does not reach the tile
+//                  border (or reaches it only through inactive crossing bonds
+//                  on the right/bottom edges) is a finished cluster: its root
+//                  (smallest site) draws the new state here (Sec. 2 (v)-(vii) /
+//                  Sec. 4 reflection) and its sites get a "closed" code.  Open
 //                  components enter the global union-find keyed by their
-//                  root's site index.  With measurement on it also counts
-//                  the bond classes of the incoming configuration (the
-//                  previous sweep's result) and the active bonds.
+//                  root's site index.
 //   k_merge        joins the open roots across every active bond that
 //                  crosses a tile edge or the periodic wrap (atomicMin,
 //                  larger root under smaller).
@@ -38,13 +40,18 @@ constexpr int TW = kTileW, TH = kTileH, NS = kTileSites, QW = kQuad;
 constexpr int kBlockThreads = kTaskWarps * 32;
 constexpr int kEnergyThreads = 256;
 constexpr unsigned FULL = 0xffffffffu;
-constexpr uint16_t kCodeFlip = 0x4000;   // closed clock cluster: reflected
-constexpr int kNone = 0x7FFFFFFF;
-constexpr int kRootFlag = 0x40000000;   // parent word of a resolved tile root: flag | code
+constexpr int kInfLabel = 1 << 20;      // "no label" (larger than any tile node)
+constexpr int kMaxPairs = 1024;         // queued unions per tile (more are joined at once)
+constexpr int kFreshList = 2 * kMaxPairs;  // fresh labels listed per tile (more: settled in place)
+// Resolved root word: kTileResolved | kResClosed | state (or kResFlip), or
+// kTileResolved | open slot.
+constexpr int kResClosed = 0x800, kResFlip = 0x400;
+static_assert(SW_MAX_Q <= 0x80 && kOpenSlots <= 0x100, "resolved words hold a state or a slot");
 
 static_assert(QW == 32, "a warp quadrant is 32 x 32: lane r owns row r as a 32-bit mask");
 static_assert(TW == 2 * QW && TH == 2 * QW, "a tile is 2 x 2 quadrants");
 static_assert(sizeof(Lattice) % 8 == 0, "lattice descriptors are copied in 8-byte words");
+static_assert(TW == 64 && kBlockThreads == NS / 32, "lane = column pair; thread t owns labels 32 t .. 32 t + 31");
 
 __device__ __forceinline__ unsigned long long read_u64(const unsigned long long *p)
 {
@@ -95,6 +102,22 @@ __device__ __forceinline__ unsigned zero_bytes4(unsigned x)
 __device__ __forceinline__ int byte_at(const uint32_t (&w)[8], int c)
 {
     return (int)((w[c >> 2] >> (8 * (c & 3))) & 0xFFu);
+}
+
+// Union of labels a and b, queued in slot idx of the tile's list, or done at
+// once when the list is full.
+__device__ __forceinline__ void queue_union(uint32_t *pairs, int idx, int a, int b, volatile uint16_t *par,
+                                            DevState *st, int where)
+{
+    if (idx < kMaxPairs) pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
+    else if (!union_t(par, a, b, kTileSites + 1)) record_error(st, kErrUnionCap, where);
+}
+
+// Per-site code of a resolved word (clock closed clusters: refined per site).
+__device__ __forceinline__ uint32_t code_of(int w)
+{
+    if (w < 0) return kCodeClosed;
+    return (w & kResClosed) ? (kCodeClosed | (uint32_t)(w & 0x7F)) : (uint32_t)(w & 0xFF);
 }
 
 __device__ __forceinline__ int reflect(int k, int m, int q)
@@ -167,46 +190,29 @@ __global__ void k_init(Lattice lat, int random)
 }
 
 // ---------------------------------------------------------------------------
-// k_label_tiles
-//
-// Per quadrant (warp):  phase A (lane r = row r) bond masks of the row;
-// phase B (lane c = column c) a scanline over the rows: every site's parent
-// word holds its run's label, a run of row y+1 takes the smallest root among
-// the runs of row y it touches (atomicMin at the run start's slot) and the
-// other touched roots are linked under it.  Tile nodes are numbered
-// row * 64 + column, which orders them like global site indices, so roots
-// stay the smallest site of their component.  Then the block joins the
-// quadrants across their inner borders, finds the roots, marks components
-// that reach the tile border, draws the closed ones and writes the codes.
+// k_bonds: the bonds of every site (Sec. 2 step (ii); clock: Sec. 4).
+// Thread = one 32-site half row of a tile: equal-neighbour masks from packed
+// byte compares, one Philox draw per two sites against the integer
+// threshold.  The masks of a tile are stored together (right bonds of its 64
+// rows, two words a row, then the down bonds), including the bonds that
+// cross into the next tile.  With measurement on it also counts the active
+// bonds and the bond classes of the incoming configuration (the previous
+// sweep's result).
 // ---------------------------------------------------------------------------
-template <bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
+template <bool MEASURE>
+__global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
 {
-    __shared__ int par[NS];
-    __shared__ uint16_t roots_all[kTaskWarps][QW * QW];
-    __shared__ unsigned int rowS_all[kTaskWarps][32], rowR_all[kTaskWarps][32], rowD_all[kTaskWarps][32];
-    __shared__ unsigned int openw[NS / 32];
-    __shared__ int s_nopen;
-    __shared__ unsigned int s_cross[kCrossWords];
     __shared__ unsigned int hist_class[SW_MAX_CLOCK_Q / 2 + 2];
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int qx = warp & 1, qy = warp >> 1;
-    uint16_t *roots = roots_all[warp];
-    unsigned int *rowS = rowS_all[warp], *rowR = rowR_all[warp], *rowD = rowD_all[warp];
-    const unsigned lanemask_lt = (1u << lane) - 1u;
-
-    unsigned int active = 0, closed_roots = 0, unequal = 0, pairs = 0;
+    unsigned int active = 0, unequal = 0, pairs = 0;
     int cur = -1;
     // Counters of lattice `cur` -> its ring rows (whole block).
     auto flush = [&]() {
         if (MEASURE && cur >= 0) {
-            unsigned long long *row = ring_row(lat, ctx.t);
-            block_add<kBlockThreads>(row + lat.q + lat.nclass, active, red);
-            block_add<kBlockThreads>(row + lat.q + lat.nclass + 1, closed_roots, red);
+            block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass, active, red);
             if (ctx.count_classes) {
                 unsigned long long *prev = ring_row(lat, ctx.t - 1);
                 if (!lat.clock) {
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                 }
             }
         }
-        active = closed_roots = unequal = pairs = 0;
+        active = unequal = pairs = 0;
         __syncthreads();
     };
 
@@ -244,243 +250,426 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int X0 = bx * TW, Y0 = by * TH;
         const int tw = min(TW, L - X0), th = min(TH, L - Y0);          // valid extent of the tile
-        const int x0 = X0 + QW * qx, y0 = Y0 + QW * qy;                // my quadrant
+        const int ry = threadIdx.x >> 1, hx = threadIdx.x & 1;          // my half row
+        const int x0 = X0 + QW * hx, y = Y0 + ry;
+        const int ncols = max(0, min(QW, tw - QW * hx));
+        const bool rv = ry < th && ncols > 0;
+        const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
+        uint32_t wd[8], dn[8], sr = 0;
+        const size_t rowbase = (size_t)y * L + x0;   // meaningful only if rv
+        {
+            const int yd = (y + 1 == L) ? 0 : y + 1;
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(lat.spin + rowbase);
+            const uint32_t *drow = reinterpret_cast<const uint32_t *>(lat.spin + (size_t)yd * L + x0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const bool ok = rv && 4 * k < ncols;
+                wd[k] = ok ? __ldg(row + k) : 0u;
+                dn[k] = ok ? __ldg(drow + k) : 0u;
+            }
+            if (rv) {
+                const int xr = (x0 + ncols == L) ? 0 : x0 + ncols;
+                sr = (uint8_t)__ldg(lat.spin + (size_t)y * L + xr);
+            }
+        }
+        unsigned eqR = 0, eqD = 0, rR = 0, rD = 0;
+        if (!clock) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
+                eqR |= zero_bytes4(wd[k] ^ __funnelshift_r(wd[k], nxt, 8)) << (4 * k);
+                eqD |= zero_bytes4(wd[k] ^ dn[k]) << (4 * k);
+            }
+        }
+        if (rv) {
+            const uint32_t pbase = (uint32_t)(rowbase >> 1);
+            if (!clock) {
+#pragma unroll
+                for (int p = 0; p < 16; ++p) {
+                    if (2 * p < ncols) {
+                        const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
+                        rR |= ((unsigned)(u.x < thr) << (2 * p)) | ((unsigned)(u.z < thr) << (2 * p + 1));
+                        rD |= ((unsigned)(u.y < thr) << (2 * p)) | ((unsigned)(u.w < thr) << (2 * p + 1));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < 16; ++p) {
+                    if (2 * p < ncols) {
+                        const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
+                        const int c0 = 2 * p, c1 = 2 * p + 1;
+                        const int s0 = byte_at(wd, c0), s1 = byte_at(wd, c1);
+                        const int s2 = (c1 + 1 < ncols) ? byte_at(wd, (c1 + 1) & 31) : (int)sr;
+                        rR |= ((unsigned)(u.x < clock_thr(lat, s0, s1, m)) << c0) |
+                              ((unsigned)(u.z < clock_thr(lat, s1, s2, m)) << c1);
+                        rD |= ((unsigned)(u.y < clock_thr(lat, s0, byte_at(dn, c0), m)) << c0) |
+                              ((unsigned)(u.w < clock_thr(lat, s1, byte_at(dn, c1), m)) << c1);
+                    }
+                }
+            }
+        }
+        const unsigned R = rv ? (clock ? (rR & V) : (rR & eqR & V)) : 0u;
+        const unsigned D = rv ? (clock ? (rD & V) : (rD & eqD & V)) : 0u;
+        if (MEASURE) {
+            active += __popc(R) + __popc(D);
+            if (ctx.count_classes) {
+                if (!clock) {
+                    if (rv) {
+                        unequal += __popc(~eqR & V) + __popc(~eqD & V);
+                        pairs += 2u * (unsigned)ncols;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const bool v = rv && c < ncols;
+                        const int s0 = byte_at(wd, c);
+                        const int s1 = (c + 1 < ncols) ? byte_at(wd, (c + 1) & 31) : (int)sr;
+                        add_hist_any(hist_class, clock_bond_class(s0, s1, q), v);
+                        add_hist_any(hist_class, clock_bond_class(s0, byte_at(dn, c), q), v);
+                    }
+                }
+            }
+        }
+        uint32_t *tb = lat.bond + (size_t)tile * kBondWords;
+        tb[threadIdx.x] = R;                  // word (row ry, half hx) of the right bonds
+        tb[kBlockThreads + threadIdx.x] = D;  // ... of the down bonds
+    }
+    flush();
+}
+
+// ---------------------------------------------------------------------------
+// k_label_tiles
+//
+// Per quadrant (warp), lane r holds row r's bond masks.  Phase B labels the
+// quadrant row by row (lane = column); queued unions, the seams between
+// quadrants and every label's root are then resolved in shared memory,
+// components that reach the tile border are marked open, closed roots draw,
+// and each site's code is written.
+// ---------------------------------------------------------------------------
+template <bool MEASURE, bool LABELS>
+__global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
+{
+    __shared__ __align__(16) uint16_t par[NS];     // union-find over labels, node v in slot tile_slot(v)
+    __shared__ __align__(16) uint16_t lbl[NS];     // label of every node at its row's scan
+    __shared__ __align__(16) uint32_t upairs[kMaxPairs];   // queued unions; then the list of roots
+    __shared__ __align__(8) unsigned int rowR[TH][2], rowD[TH][2];
+    __shared__ unsigned int openw[NS / 32];
+    __shared__ int s_nopen, s_npairs, s_wsum[kTaskWarps];
+    __shared__ unsigned int s_cross[kCrossWords];
+    __shared__ unsigned int red[32];
+    __shared__ __align__(16) Lattice lat;
+    __shared__ TaskCtx ctx;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qx = warp & 1, qy = warp >> 1;
+
+    unsigned int closed_roots = 0;
+    int cur = -1;
+    if (threadIdx.x < kCrossWords) s_cross[threadIdx.x] = 0u;   // before the first barrier below
+    // Counters of lattice `cur` -> its ring row (whole block).
+    auto flush = [&]() {
+        if (MEASURE && cur >= 0) block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass + 1, closed_roots, red);
+        closed_roots = 0;
+        __syncthreads();
+    };
+
+    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
+        const int rep = find_rep(b.task_off, b.nrep, task);
+        if (rep != cur) {
+            flush();
+            load_lattice(&lat, b.lat + rep);
+            __syncthreads();
+            if (threadIdx.x == 0) ctx = task_context<MEASURE>(lat);
+            __syncthreads();
+            cur = rep;
+        }
+        const int tile = task - __ldg(b.task_off + rep);
+        const int L = lat.L, q = lat.q;
+        const bool clock = lat.clock != 0;
+        const unsigned long long t = ctx.t;
+        const int m = ctx.m;
+        const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
+        const int X0 = bx * TW, Y0 = by * TH;
+        const int tw = min(TW, L - X0), th = min(TH, L - Y0);          // valid extent of the tile
         const int ncols = max(0, min(QW, tw - QW * qx));
         const int nrows = max(0, min(QW, th - QW * qy));
         const bool qa = ncols > 0 && nrows > 0;                        // quadrant has sites (warp-uniform)
         const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
         const bool ext_right = QW * qx + ncols == tw;                   // my right edge is the tile's
         const bool ext_bottom = QW * qy + nrows == th;
-        const int nb = (QW * qy) * TW + QW * qx;                        // node of my quadrant's corner
         unsigned rc_bits = 0, dc_bits = 0;
+        unsigned Rq = 0, Dq = 0;   // lane r: row r's bonds inside the quadrant (right, down)
 
         for (int i = threadIdx.x; i < NS / 32; i += blockDim.x) openw[i] = 0u;
-        if (threadIdx.x == 0) s_nopen = 0;
-        if (threadIdx.x < kCrossWords) s_cross[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) s_nopen = s_npairs = 0;
 
-        // ===== phase A: lane = row ==========================================
+        // ===== bond masks of my quadrant (written by k_bonds), lane = row ======
         if (qa) {
             const int r = lane;
             const bool rv = r < nrows;
-            const int y = y0 + r;
-            const size_t rowbase = (size_t)y * L + x0;   // meaningful only if rv
-            uint32_t wd[8], dn[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                wd[k] = (rv && 4 * k < ncols) ? __ldg(reinterpret_cast<const uint32_t *>(lat.spin + rowbase) + k) : 0u;
-            uint32_t sr = 0;
-            if (rv) {
-                const int xr = (x0 + ncols == L) ? 0 : x0 + ncols;
-                sr = (uint8_t)__ldg(lat.spin + (size_t)y * L + xr);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) dn[k] = __shfl_down_sync(FULL, wd[k], 1);
-            if (rv && r == nrows - 1) {
-                const int yd = (y + 1 == L) ? 0 : y + 1;
-                const uint32_t *drow = reinterpret_cast<const uint32_t *>(lat.spin + (size_t)yd * L + x0);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) dn[k] = (4 * k < ncols) ? __ldg(drow + k) : 0u;
-            }
-            unsigned eqR = 0, eqD = 0, rR = 0, rD = 0;
-            if (!clock) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
-                    eqR |= zero_bytes4(wd[k] ^ __funnelshift_r(wd[k], nxt, 8)) << (4 * k);
-                    eqD |= zero_bytes4(wd[k] ^ dn[k]) << (4 * k);
-                }
-            }
-            if (rv) {
-                const uint32_t pbase = (uint32_t)(rowbase >> 1);
-                if (!clock) {
-#pragma unroll
-                    for (int p = 0; p < 16; ++p) {
-                        if (2 * p < ncols) {
-                            const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
-                            rR |= ((unsigned)(u.x < thr) << (2 * p)) | ((unsigned)(u.z < thr) << (2 * p + 1));
-                            rD |= ((unsigned)(u.y < thr) << (2 * p)) | ((unsigned)(u.w < thr) << (2 * p + 1));
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int p = 0; p < 16; ++p) {
-                        if (2 * p < ncols) {
-                            const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
-                            const int c0 = 2 * p, c1 = 2 * p + 1;
-                            const int s0 = byte_at(wd, c0), s1 = byte_at(wd, c1);
-                            const int s2 = (c1 + 1 < ncols) ? byte_at(wd, (c1 + 1) & 31) : (int)sr;
-                            rR |= ((unsigned)(u.x < clock_thr(lat, s0, s1, m)) << c0) |
-                                  ((unsigned)(u.z < clock_thr(lat, s1, s2, m)) << c1);
-                            rD |= ((unsigned)(u.y < clock_thr(lat, s0, byte_at(dn, c0), m)) << c0) |
-                                  ((unsigned)(u.w < clock_thr(lat, s1, byte_at(dn, c1), m)) << c1);
-                        }
-                    }
-                }
-            }
-            const unsigned R = clock ? (rR & V) : (rR & eqR & V);
-            const unsigned D = clock ? (rD & V) : (rD & eqD & V);
-
-            if (MEASURE) {
-                if (rv) active += __popc(R) + __popc(D);
-                if (ctx.count_classes) {
-                    if (!clock) {
-                        if (rv) {
-                            unequal += __popc(~eqR & V) + __popc(~eqD & V);
-                            pairs += 2u * (unsigned)ncols;
-                        }
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            const bool v = rv && c < ncols;
-                            const int s0 = byte_at(wd, c);
-                            const int s1 = (c + 1 < ncols) ? byte_at(wd, (c + 1) & 31) : (int)sr;
-                            add_hist_any(hist_class, clock_bond_class(s0, s1, q), v);
-                            add_hist_any(hist_class, clock_bond_class(s0, byte_at(dn, c), q), v);
-                        }
-                    }
-                }
-            }
-            const unsigned Rint = R & (V >> 1);   // both ends inside the quadrant
-            rowS[r] = rv ? (V & ~(Rint << 1)) : 0u;
-            rowR[r] = Rint;
-            rowD[r] = (r + 1 < nrows) ? D : 0u;
+            const uint32_t *tb = lat.bond + (size_t)tile * kBondWords + (QW * qy + r) * 2 + qx;
+            const unsigned R = rv ? __ldg(tb) : 0u;
+            const unsigned D = rv ? __ldg(tb + kBlockThreads) : 0u;
             rc_bits = __ballot_sync(FULL, rv && ((R >> (ncols - 1)) & 1u));   // bonds leaving the right edge
             dc_bits = __shfl_sync(FULL, D, nrows - 1);                       // bonds leaving the bottom edge
-            __syncwarp();
-
-            // ===== phase B: lane = column, scanline over the rows ============
-            const int c = lane;
-            const bool cv = c < ncols;
-            const unsigned upto_c = FULL >> (31 - c);   // columns <= c
-            unsigned S = rowS[0], Rr = rowR[0];
-            par[nb + c] = nb + (cv ? 31 - __clz(S & upto_c) : c);
-            for (int row = 0; row + 1 < nrows; ++row) {
-                const unsigned Sn = rowS[row + 1], Rn = rowR[row + 1], D2 = rowD[row];
-                // A vertical bond is implied by its left neighbour column when
-                // both rows are joined across that column pair.
-                const unsigned E = D2 & ~((D2 & Rr & Rn) << 1);
-                const int base1 = nb + (row + 1) * TW;
-                const int s = cv ? 31 - __clz(Sn & upto_c) : c;   // start of my run in row + 1
-                par[base1 + c] = kNone;
-                int cand = kNone;
-                if ((E >> c) & 1u) {
-                    cand = find_s(par, nb + row * TW + c, NS + 1);
-                    if (cand < 0) {
-                        record_error(lat.st, kErrFindCap, Y0 * L + X0);
-                        cand = kNone;
-                    }
-                }
-                __syncwarp();
-                // Smallest root touched by my run, collected at the run start's slot.
-                if (cand != kNone) atomicMin(&par[base1 + s], cand);
-                __syncwarp();
-                int mm = par[base1 + s];
-                if (mm == kNone) mm = base1 + s;
-                if (cand != kNone && cand != mm && !union_s(par, cand, mm, NS + 1))
-                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
-                __syncwarp();
-                par[base1 + c] = mm;
-                __syncwarp();
-                S = Sn;
-                Rr = Rn;
-            }
-        }
-        __syncthreads();
-
-        // ===== join the quadrants across their inner borders ==================
-        if (qa) {
-            if (!ext_right && lane < nrows && ((rc_bits >> lane) & 1u))
-                if (!union_s(par, nb + lane * TW + QW - 1, nb + lane * TW + QW, NS + 1))
-                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
-            if (!ext_bottom && lane < ncols && ((dc_bits >> lane) & 1u))
-                if (!union_s(par, nb + (QW - 1) * TW + lane, nb + QW * TW + lane, NS + 1))
-                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
-        }
-        __syncthreads();
-
-        // ===== roots, tile-border components, draws, codes ====================
-        const int c = lane;
-        const bool cv = c < ncols;
-        int nroots = 0;
-        if (qa) {
-            // A node is a root iff its parent word is itself (unions only ever
-            // re-point roots).  Collect my quadrant's roots in row order.
-            for (int row = 0; row < nrows; ++row) {
-                const int x = nb + row * TW + c;
-                const bool isroot = cv && par[x] == x;
-                const unsigned bal = __ballot_sync(FULL, isroot);
-                if (isroot) roots[nroots + __popc(bal & lanemask_lt)] = (uint16_t)x;
-                nroots += __popc(bal);
-            }
-            // Components reaching the tile border.  Left and top edges always
-            // count (their bonds belong to the neighbouring tiles); right and
-            // bottom edges count through an active crossing bond.
-            int site[4];
-            bool want[4];
-            want[0] = qy == 0 && cv;                                       // top row
-            site[0] = nb + c;
-            want[1] = qx == 0 && c < nrows;                                // left column
-            site[1] = nb + c * TW;
-            want[2] = ext_right && c < nrows && ((rc_bits >> c) & 1u);     // right edge, row c
-            site[2] = nb + c * TW + ncols - 1;
-            want[3] = ext_bottom && cv && ((dc_bits >> c) & 1u);           // bottom edge, column c
-            site[3] = nb + (nrows - 1) * TW + c;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (!want[k]) continue;
-                const int root = find_s(par, site[k], NS + 1);
-                if (root < 0) {
-                    record_error(lat.st, kErrFindCap, Y0 * L + X0);
-                    continue;
-                }
-                atomicOr(&openw[root >> 5], 1u << (root & 31));
-            }
+            // Tile-internal bonds as 64-bit rows (two 32-bit halves): the
+            // right bond of the tile's last column and the down bonds of its
+            // last row cross into the neighbouring tiles.
+            const unsigned Rin = R & (ext_right ? (V >> 1) : V);
+            const unsigned Din = (ext_bottom && r == nrows - 1) ? 0u : D;
+            rowR[QW * qy + r][qx] = rv ? Rin : 0u;
+            rowD[QW * qy + r][qx] = rv ? Din : 0u;
+            Rq = rv ? (R & (V >> 1)) : 0u;             // both ends in the quadrant
+            Dq = (r + 1 < nrows) ? D : 0u;
             if (lane == 0) {
                 if (ext_right) atomicOr(&s_cross[qy], rc_bits);
                 if (ext_bottom) atomicOr(&s_cross[2 + qx], dc_bits);
             }
+        } else {
+            rowR[QW * qy + lane][qx] = 0u;
+            rowD[QW * qy + lane][qx] = 0u;
         }
         __syncthreads();
-        // Closed roots draw now; open roots join the global union-find.  The
-        // result is stored in the root's own parent word, flagged.
-        for (int j = c; j < nroots; j += 32) {
-            const int x = roots[j];
-            const int g = tile_site(L, bx, by, x);
-            int code;
-            if ((openw[x >> 5] >> (x & 31)) & 1u) {
+
+        // ===== phase B: labels, quadrant by quadrant (warp), lane = column ======
+        // Row by row, every site carries the label of the site above it when
+        // the two are bonded.  A run (maximal horizontally bonded segment of
+        // the row) takes the label carried by its first such site; a run with
+        // none opens a fresh label, its first node.  Other labels carried into
+        // the run are queued for a union with the run's.  Labels are tile
+        // nodes row * 64 + column, which order like global site indices, so
+        // with unions linking larger roots under smaller each component's
+        // root is its smallest site.
+        if (qa) {
+            const int c = lane;
+            const bool cv = c < ncols;
+            const unsigned upto = FULL >> (31 - c);   // columns <= c
+            const unsigned lanes_lt = (1u << lane) - 1u;
+            const int nb = (QW * qy) * TW + QW * qx;  // node of the quadrant's corner
+            int pl = kInfLabel;                       // label of the site above
+            unsigned Dp = 0u, Rp = 0u;
+            for (int row = 0; row < nrows; ++row) {
+                const unsigned Rr = __shfl_sync(FULL, Rq, row);
+                const unsigned S = ~(Rr << 1);                       // run starts
+                const int s0 = 31 - __clz(S & upto);                 // my run's first column
+                const unsigned nxt = S & ~upto;                      // starts right of me
+                const unsigned run = (nxt ? (nxt & (0u - nxt)) - 1u : FULL) & ~((1u << s0) - 1u);
+                const int cand = ((Dp >> c) & 1u) ? pl : kInfLabel;
+                const unsigned hasc = __ballot_sync(FULL, cand != kInfLabel) & run;
+                int mlab = __shfl_sync(FULL, cand, hasc ? __ffs(hasc) - 1 : c);
+                const int node = nb + row * TW + c;
+                if (mlab == kInfLabel) mlab = node - (c - s0);       // fresh: the run's first node
+                if (cv) {
+                    if (mlab == node) par[tile_slot(node)] = (uint16_t)node;
+                    lbl[node] = (uint16_t)mlab;
+                }
+                // A bond whose left neighbour joins the same two runs is skipped.
+                const unsigned E = Dp & ~((Dp & Rp & Rr) << 1);
+                const bool u = cv && ((E >> c) & 1u) && cand != mlab;
+                const unsigned bu = __ballot_sync(FULL, u);
+                if (bu) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&s_npairs, __popc(bu));
+                    base = __shfl_sync(FULL, base, 0);
+                    if (u) queue_union(upairs, base + __popc(bu & lanes_lt), cand, mlab, par, lat.st, Y0 * L + X0);
+                }
+                __syncwarp();
+                pl = mlab;
+                Rp = Rr;
+                Dp = __shfl_sync(FULL, Dq, row);
+            }
+        }
+        __syncthreads();
+
+        // ===== unions: queued pairs, then the seams between the quadrants =====
+        {
+            const int np = min(s_npairs, kMaxPairs);
+            const int nitems = np + TH + TW;
+            for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+                int a, c;
+                if (i < np) {
+                    const uint32_t pr = upairs[i];
+                    a = (int)(pr & 0xFFFFu);
+                    c = (int)(pr >> 16);
+                } else if (i < np + TH) {   // column 31 - 32 of row y
+                    const int y = i - np;
+                    if (y >= th || tw <= QW || !((rowR[y][0] >> 31) & 1u)) continue;
+                    a = lbl[y * TW + QW - 1];
+                    c = lbl[y * TW + QW];
+                } else {                     // row 31 - 32 of column x
+                    const int x = i - np - TH;
+                    if (x >= tw || th <= QW || !((rowD[QW - 1][x >> 5] >> (x & 31)) & 1u)) continue;
+                    a = lbl[(QW - 1) * TW + x];
+                    c = lbl[QW * TW + x];
+                }
+                if (!union_t(par, a, c, NS + 1)) record_error(lat.st, kErrUnionCap, Y0 * L + X0);
+            }
+        }
+        __syncthreads();
+
+        // ===== fresh labels into one list; components reaching the border ======
+        // Fresh labels are the nodes that are their own label.  Thread t owns
+        // nodes 32 t .. 32 t + 31 (row t / 2).
+        unsigned fresh = 0;
+        {
+            const int vrow = threadIdx.x >> 1, vcol = 32 * (threadIdx.x & 1);
+            if (vrow < th && vcol < tw) {
+                const uint4 *lp = reinterpret_cast<const uint4 *>(lbl) + 4 * threadIdx.x;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint4 w4 = lp[k];
+                    const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int j = 8 * k + 2 * h;
+                        const uint32_t v = 32u * threadIdx.x + (uint32_t)j;
+                        fresh |= ((unsigned)((ws[h] & 0xFFFFu) == v) << j) | ((unsigned)((ws[h] >> 16) == v + 1u) << (j + 1));
+                    }
+                }
+                const int ncol = min(32, tw - vcol);
+                fresh &= ncol >= 32 ? FULL : ((1u << ncol) - 1u);
+            }
+        }
+        // Left and top edges always make a component open (their bonds belong
+        // to the neighbouring tiles); right and bottom edges through an active
+        // crossing bond.  Items: top row, left column, right column, bottom row.
+        for (int item = threadIdx.x; item < 4 * TW; item += blockDim.x) {
+            const int side = item / TW, k = item % TW;
+            int node = -1;
+            if (side == 0) {
+                if (k < tw) node = k;
+            } else if (side == 1) {
+                if (k < th) node = k * TW;
+            } else if (side == 2) {
+                if (k < th && ((s_cross[k >> 5] >> (k & 31)) & 1u)) node = k * TW + tw - 1;
+            } else {
+                if (k < tw && ((s_cross[2 + (k >> 5)] >> (k & 31)) & 1u)) node = (th - 1) * TW + k;
+            }
+            if (node < 0) continue;
+            const int root = find_t(par, lbl[node], NS + 1);
+            if (root < 0) {
+                record_error(lat.st, kErrFindCap, Y0 * L + X0);
+                continue;
+            }
+            atomicOr(&openw[root >> 5], 1u << (root & 31));
+        }
+        const int nmine = __popc(fresh);
+        int incl = nmine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += o;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        int nfresh = 0, off = incl - nmine;
+#pragma unroll
+        for (int w = 0; w < kTaskWarps; ++w) {
+            off += w < warp ? s_wsum[w] : 0;
+            nfresh += s_wsum[w];
+        }
+        const bool listed = nfresh <= kFreshList;   // block-uniform
+        uint16_t *flist = reinterpret_cast<uint16_t *>(upairs);
+        if (listed) {
+            unsigned f2 = fresh;
+            while (f2) {
+                const int bit = __ffs(f2) - 1;
+                f2 &= f2 - 1;
+                flist[off++] = (uint16_t)(32 * threadIdx.x + bit);
+            }
+        }
+        __syncthreads();
+
+        // ===== settle: roots draw (closed) or take an open slot; every other
+        // fresh label is pointed straight at its root.  A root's parent word
+        // becomes resolved (it carries the outcome).
+        auto settle = [&](int v) {
+            int x = v;
+            for (int it = 0; it <= NS; ++it) {   // read-only chase: stops at a root, settled or not
+                const int p = par_ld(par, x);
+                if (p == x || p >= kTileResolved) break;
+                x = p;
+            }
+            if (x != v) {
+                par[tile_slot(v)] = (uint16_t)x;
+                return;
+            }
+            const int g = tile_site(L, bx, by, v);
+            int w;
+            if ((openw[v >> 5] >> (v & 31)) & 1u) {
                 const int slot = atomicAdd(&s_nopen, 1);
-                lat.open_list[(size_t)tile * kOpenSlots + slot] = g;
-                lat.label[g] = g;
-                code = slot;
+                if (slot < kOpenSlots) {   // at most 2 * (64 + 64) - 4 open components
+                    lat.open_list[(size_t)tile * kOpenSlots + slot] = g;
+                    lat.label[g] = g;
+                    w = kTileResolved | slot;
+                } else {
+                    record_error(lat.st, kErrInternal, g);
+                    w = kTileResolved | kResClosed;
+                }
             } else {
                 const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
-                code = clock ? (kCodeClosed | ((u >> 31) ? kCodeFlip : 0)) : (kCodeClosed | mulhi_q(u, q));
+                w = kTileResolved | kResClosed | (clock ? ((u >> 31) ? kResFlip : 0) : mulhi_q(u, q));
                 ++closed_roots;
             }
-            par[x] = kRootFlag | code;
-        }
-        __syncthreads();
-        if (qa && cv) {
-            for (int row = 0; row < nrows; ++row) {
-                const size_t site = (size_t)(y0 + row) * L + x0 + c;
-                // Follow parents to the flagged root word.
-                int x = nb + row * TW + c;
-                int p = par[x];
-                for (int it = 0; it < NS && !(p & kRootFlag); ++it) {
-                    x = p;
-                    p = par[x];
-                }
-                uint32_t code = (uint32_t)p & 0xFFFFu;
-                if (clock && (code & kCodeClosed)) {
-                    const int k0 = valid_state(__ldg(lat.spin + site), q);
-                    code = kCodeClosed | (uint32_t)((code & kCodeFlip) ? reflect(k0, m, q) : k0);
-                }
-                if (LABELS && (code & kCodeClosed)) lat.label[site] = tile_site(L, bx, by, x);
-                lat.code[site] = (uint16_t)code;
+            par[tile_slot(v)] = (uint16_t)w;
+        };
+        if (listed) {
+            for (int i = threadIdx.x; i < nfresh; i += blockDim.x) settle(flist[i]);
+        } else {
+            while (fresh) {
+                const int bit = __ffs(fresh) - 1;
+                fresh &= fresh - 1;
+                settle(32 * threadIdx.x + bit);
             }
         }
-        if (threadIdx.x == 0) lat.open_count[tile] = s_nopen;
-        if (threadIdx.x < kCrossWords) lat.cross[(size_t)tile * kCrossWords + threadIdx.x] = s_cross[threadIdx.x];
+        __syncthreads();
+
+        // ===== codes: lane = column pair, one row per warp step ================
+        const int c0 = 2 * lane;
+        if (c0 < tw) {   // tw % 4 == 0: both columns or neither
+            for (int row = warp; row < th; row += kTaskWarps) {
+                const uint32_t lp = reinterpret_cast<const uint32_t *>(lbl)[(row * TW + c0) >> 1];
+                // A label's word is resolved (a root) or names its root.
+                int x0n = (int)(lp & 0xFFFFu), x1n = (int)(lp >> 16);
+                int w0 = par_ld(par, x0n), w1 = par_ld(par, x1n);
+                if (w0 < kTileResolved) {
+                    x0n = w0;
+                    w0 = par_ld(par, w0);
+                }
+                if (w1 < kTileResolved) {
+                    x1n = w1;
+                    w1 = par_ld(par, w1);
+                }
+                if (w0 < kTileResolved || w1 < kTileResolved) {   // unreachable for a settled tile
+                    record_error(lat.st, kErrInternal, Y0 * L + X0);
+                    w0 = w1 = -1;
+                }
+                const size_t site = (size_t)(Y0 + row) * L + X0 + c0;
+                uint32_t code0 = code_of(w0), code1 = code_of(w1);
+                if (clock && ((code0 | code1) & kCodeClosed)) {
+                    const char2 k2 = *reinterpret_cast<const char2 *>(lat.spin + site);
+                    if (code0 & kCodeClosed) {
+                        const int k0 = valid_state(k2.x, q);
+                        code0 = kCodeClosed | (uint32_t)((w0 & kResFlip) ? reflect(k0, m, q) : k0);
+                    }
+                    if (code1 & kCodeClosed) {
+                        const int k1 = valid_state(k2.y, q);
+                        code1 = kCodeClosed | (uint32_t)((w1 & kResFlip) ? reflect(k1, m, q) : k1);
+                    }
+                }
+                if (LABELS) {
+                    if (code0 & kCodeClosed) lat.label[site] = tile_site(L, bx, by, x0n);
+                    if (code1 & kCodeClosed) lat.label[site + 1] = tile_site(L, bx, by, x1n);
+                }
+                *reinterpret_cast<uint32_t *>(lat.code + site) = code0 | (code1 << 16);
+            }
+        }
+        if (threadIdx.x == 0) lat.open_count[tile] = min(s_nopen, kOpenSlots);
+        if (threadIdx.x < kCrossWords) {
+            // Zeroed by its only reader, ready for the next task.
+            lat.cross[(size_t)tile * kCrossWords + threadIdx.x] = s_cross[threadIdx.x];
+            s_cross[threadIdx.x] = 0u;
+        }
         __syncthreads();
     }
     flush();
@@ -827,9 +1016,10 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
     auto mark = [&]() {
         if (ev) cudaEventRecord(ev[nev++], s);
     };
-    const int blocks = std::max(1, std::min(b.ntasks, sm_count * shape.label));
     mark();
-    k_label_tiles<MEASURE, LABELS><<<blocks, kBlockThreads, 0, s>>>(b);
+    k_bonds<MEASURE><<<std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM)), kBlockThreads, 0, s>>>(b);
+    mark();
+    k_label_tiles<MEASURE, LABELS><<<std::max(1, std::min(b.ntasks, sm_count * shape.label)), kBlockThreads, 0, s>>>(b);
     mark();
     const int mblocks =
         (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * shape.merge));

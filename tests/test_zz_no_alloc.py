@@ -46,8 +46,9 @@ def noalloc(L, q, model, T, seed, sweep0, n, spins, counts):
 
 
 # The largest lattice runs first, so later cases start from an array that
-# holds another lattice's leftovers.  n2 = 300 spans more counter rows than
-# one chunk (255 sweeps) and wraps the row ring.
+# holds another lattice's leftovers.  n2 = 300 spans more sweeps than the
+# array's counter rows hold at once, so the call drains them in chunks and
+# wraps the row ring.
 CASES = [
     (sw.SW_NOALLOC_MAX_L, 2, sw.SW_POTTS, tc_potts(2), 14, 3, 2),
     (64, 2, sw.SW_ISING, TC_ISING, 11, 7, 5),
