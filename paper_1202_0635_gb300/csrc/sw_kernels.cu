@@ -261,11 +261,22 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
             const int yd = (y + 1 == L) ? 0 : y + 1;
             const uint32_t *row = reinterpret_cast<const uint32_t *>(lat.spin + rowbase);
             const uint32_t *drow = reinterpret_cast<const uint32_t *>(lat.spin + (size_t)yd * L + x0);
+            if ((L & 15) == 0 && ncols == QW) {   // whole half row, 16-byte aligned
+                const uint4 a0 = rv ? __ldg(reinterpret_cast<const uint4 *>(row)) : make_uint4(0, 0, 0, 0);
+                const uint4 a1 = rv ? __ldg(reinterpret_cast<const uint4 *>(row) + 1) : make_uint4(0, 0, 0, 0);
+                const uint4 b0 = rv ? __ldg(reinterpret_cast<const uint4 *>(drow)) : make_uint4(0, 0, 0, 0);
+                const uint4 b1 = rv ? __ldg(reinterpret_cast<const uint4 *>(drow) + 1) : make_uint4(0, 0, 0, 0);
+                wd[0] = a0.x; wd[1] = a0.y; wd[2] = a0.z; wd[3] = a0.w;
+                wd[4] = a1.x; wd[5] = a1.y; wd[6] = a1.z; wd[7] = a1.w;
+                dn[0] = b0.x; dn[1] = b0.y; dn[2] = b0.z; dn[3] = b0.w;
+                dn[4] = b1.x; dn[5] = b1.y; dn[6] = b1.z; dn[7] = b1.w;
+            } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const bool ok = rv && 4 * k < ncols;
-                wd[k] = ok ? __ldg(row + k) : 0u;
-                dn[k] = ok ? __ldg(drow + k) : 0u;
+                for (int k = 0; k < 8; ++k) {
+                    const bool ok = rv && 4 * k < ncols;
+                    wd[k] = ok ? __ldg(row + k) : 0u;
+                    dn[k] = ok ? __ldg(drow + k) : 0u;
+                }
             }
             if (rv) {
                 const int xr = (x0 + ncols == L) ? 0 : x0 + ncols;
@@ -354,6 +365,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
     __shared__ __align__(16) uint32_t upairs[kMaxPairs];   // queued unions; then the list of roots
     __shared__ __align__(8) unsigned int rowR[TH][2], rowD[TH][2];
     __shared__ unsigned int openw[NS / 32];
+    __shared__ int rmin_all[kTaskWarps][QW];                // per-warp run minima of the scan
     __shared__ int s_nopen, s_npairs, s_wsum[kTaskWarps];
     __shared__ unsigned int s_cross[kCrossWords];
     __shared__ unsigned int red[32];
@@ -443,35 +455,47 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         if (qa) {
             const int c = lane;
             const bool cv = c < ncols;
+            const unsigned bit = 1u << c;
             const unsigned upto = FULL >> (31 - c);   // columns <= c
-            const unsigned lanes_lt = (1u << lane) - 1u;
+            const unsigned lanes_lt = bit - 1u;
             const int nb = (QW * qy) * TW + QW * qx;  // node of the quadrant's corner
-            int pl = kInfLabel;                       // label of the site above
+            int *rmin = rmin_all[warp];
+            int pl = 0;                               // label of the site above (valid where Dp has my bit)
+            uint32_t lastq = 0xFFFFFFFFu;             // pair this lane queued last
             unsigned Dp = 0u, Rp = 0u;
             for (int row = 0; row < nrows; ++row) {
                 const unsigned Rr = __shfl_sync(FULL, Rq, row);
                 const unsigned S = ~(Rr << 1);                       // run starts
                 const int s0 = 31 - __clz(S & upto);                 // my run's first column
-                const unsigned nxt = S & ~upto;                      // starts right of me
-                const unsigned run = (nxt ? (nxt & (0u - nxt)) - 1u : FULL) & ~((1u << s0) - 1u);
-                const int cand = ((Dp >> c) & 1u) ? pl : kInfLabel;
-                const unsigned hasc = __ballot_sync(FULL, cand != kInfLabel) & run;
-                int mlab = __shfl_sync(FULL, cand, hasc ? __ffs(hasc) - 1 : c);
+                // The run takes the smallest label a bond from above carries
+                // into it (collected at its first column), else a fresh
+                // label: its first node.
+                rmin[c] = kInfLabel;
+                __syncwarp();
+                if (Dp & bit) atomicMin(&rmin[s0], pl);
+                __syncwarp();
                 const int node = nb + row * TW + c;
-                if (mlab == kInfLabel) mlab = node - (c - s0);       // fresh: the run's first node
+                const int up = rmin[s0];
+                const int mlab = up != kInfLabel ? up : node - (c - s0);
                 if (cv) {
-                    if (mlab == node) par[tile_slot(node)] = (uint16_t)node;
+                    if (mlab == node) par[node ^ row] = (uint16_t)node;   // tile_slot(node): row < 32
                     lbl[node] = (uint16_t)mlab;
                 }
-                // A bond whose left neighbour joins the same two runs is skipped.
+                // A bond from above carrying another label queues a union,
+                // unless its left neighbour joins the same two runs or this
+                // lane queued the same pair last.
                 const unsigned E = Dp & ~((Dp & Rp & Rr) << 1);
-                const bool u = cv && ((E >> c) & 1u) && cand != mlab;
+                const uint32_t pair = (uint32_t)pl | ((uint32_t)mlab << 16);
+                const bool u = (E & bit) && pl != mlab && pair != lastq;
                 const unsigned bu = __ballot_sync(FULL, u);
                 if (bu) {
                     int base = 0;
                     if (lane == 0) base = atomicAdd(&s_npairs, __popc(bu));
                     base = __shfl_sync(FULL, base, 0);
-                    if (u) queue_union(upairs, base + __popc(bu & lanes_lt), cand, mlab, par, lat.st, Y0 * L + X0);
+                    if (u) {
+                        queue_union(upairs, base + __popc(bu & lanes_lt), pl, mlab, par, lat.st, Y0 * L + X0);
+                        lastq = pair;
+                    }
                 }
                 __syncwarp();
                 pl = mlab;
@@ -616,10 +640,29 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         if (listed) {
             for (int i = threadIdx.x; i < nfresh; i += blockDim.x) settle(flist[i]);
         } else {
+            unsigned f2 = fresh;
+            while (f2) {
+                const int bit = __ffs(f2) - 1;
+                f2 &= f2 - 1;
+                settle(32 * threadIdx.x + bit);
+            }
+        }
+        __syncthreads();
+        // Every other fresh label takes its root's resolved word, so that a
+        // site's label leads to its outcome in one step.  The roots' words
+        // are only read here.  (Debug labels keep the root's index instead.)
+        auto adopt = [&](int v) {
+            const int p = par_ld(par, v);
+            if (p < kTileResolved) par[tile_slot(v)] = (uint16_t)par_ld(par, p);
+        };
+        if (LABELS) {
+        } else if (listed) {
+            for (int i = threadIdx.x; i < nfresh; i += blockDim.x) adopt(flist[i]);
+        } else {
             while (fresh) {
                 const int bit = __ffs(fresh) - 1;
                 fresh &= fresh - 1;
-                settle(32 * threadIdx.x + bit);
+                adopt(32 * threadIdx.x + bit);
             }
         }
         __syncthreads();
@@ -629,16 +672,17 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         if (c0 < tw) {   // tw % 4 == 0: both columns or neither
             for (int row = warp; row < th; row += kTaskWarps) {
                 const uint32_t lp = reinterpret_cast<const uint32_t *>(lbl)[(row * TW + c0) >> 1];
-                // A label's word is resolved (a root) or names its root.
                 int x0n = (int)(lp & 0xFFFFu), x1n = (int)(lp >> 16);
                 int w0 = par_ld(par, x0n), w1 = par_ld(par, x1n);
-                if (w0 < kTileResolved) {
-                    x0n = w0;
-                    w0 = par_ld(par, w0);
-                }
-                if (w1 < kTileResolved) {
-                    x1n = w1;
-                    w1 = par_ld(par, w1);
+                if (LABELS) {   // a label's word is resolved (a root) or names its root
+                    if (w0 < kTileResolved) {
+                        x0n = w0;
+                        w0 = par_ld(par, w0);
+                    }
+                    if (w1 < kTileResolved) {
+                        x1n = w1;
+                        w1 = par_ld(par, w1);
+                    }
                 }
                 if (w0 < kTileResolved || w1 < kTileResolved) {   // unreachable for a settled tile
                     record_error(lat.st, kErrInternal, Y0 * L + X0);
