@@ -134,13 +134,6 @@ __device__ __forceinline__ int clock_bond_class(int a, int b, int q)
     return dk < q - dk ? dk : q - dk;
 }
 
-__device__ __forceinline__ uint32_t clock_thr(const Lattice &lat, int a, int b, int m)
-{
-    const int n2 = 2 * lat.q;
-    return __ldg(lat.thr_tab + clock_class(valid_state(a, lat.q), m, lat.q) * n2 +
-                 clock_class(valid_state(b, lat.q), m, lat.q));
-}
-
 // Shared histogram for any number of bins (warp-aggregated atomics).
 // Must be called by all 32 lanes of the warp; invalid lanes add nothing.
 __device__ __forceinline__ void add_hist_any(unsigned int *hist, int v, bool valid)
@@ -202,6 +195,11 @@ __global__ void k_init(Lattice lat, int random)
 template <bool MEASURE>
 __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
 {
+    // Clock model: threshold of two projection magnitudes r_a, r_b on the
+    // same side of the sweep's mirror axis, and each state's projection
+    // (magnitude r = j mod q, side 1 or 2 in bits 6-7, 0 on the axis).
+    __shared__ uint32_t s_thr[SW_MAX_CLOCK_Q * SW_MAX_CLOCK_Q];
+    __shared__ uint8_t s_proj[SW_MAX_CLOCK_Q];
     __shared__ unsigned int hist_class[SW_MAX_CLOCK_Q / 2 + 2];
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
@@ -239,14 +237,31 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
             if (MEASURE)
                 for (int k = threadIdx.x; k < SW_MAX_CLOCK_Q / 2 + 2; k += blockDim.x) hist_class[k] = 0u;
             __syncthreads();
+            if (lat.clock) {
+                const int q = lat.q;
+                for (int i = threadIdx.x; i < q * q; i += blockDim.x)
+                    s_thr[i] = __ldg(lat.thr_tab + (i / q) * (2 * q) + (i % q));
+                for (int k = threadIdx.x; k < q; k += blockDim.x) {
+                    const int j = clock_class(k, ctx.m, q);
+                    const int side = (j == 0 || j == q) ? 0 : (j < q ? 1 : 2);
+                    s_proj[k] = (uint8_t)((j % q) | (side << 6));
+                }
+                __syncthreads();
+            }
             cur = rep;
         }
         const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
         const bool clock = lat.clock != 0;
         const unsigned long long t = ctx.t;
-        const int m = ctx.m;
         const uint32_t thr = lat.thr;
+        // Clock bond threshold of states a, b (zero unless both project
+        // strictly onto the same side of the axis).
+        auto cthr = [&](int a, int c) -> uint32_t {
+            const int pa = s_proj[valid_state(a, q)], pc = s_proj[valid_state(c, q)];
+            if (((pa ^ pc) & 0xC0) || !(pa & 0xC0)) return 0u;
+            return s_thr[(pa & 63) * q + (pc & 63)];
+        };
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int X0 = bx * TW, Y0 = by * TH;
         const int tw = min(TW, L - X0), th = min(TH, L - Y0);          // valid extent of the tile
@@ -311,10 +326,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                         const int c0 = 2 * p, c1 = 2 * p + 1;
                         const int s0 = byte_at(wd, c0), s1 = byte_at(wd, c1);
                         const int s2 = (c1 + 1 < ncols) ? byte_at(wd, (c1 + 1) & 31) : (int)sr;
-                        rR |= ((unsigned)(u.x < clock_thr(lat, s0, s1, m)) << c0) |
-                              ((unsigned)(u.z < clock_thr(lat, s1, s2, m)) << c1);
-                        rD |= ((unsigned)(u.y < clock_thr(lat, s0, byte_at(dn, c0), m)) << c0) |
-                              ((unsigned)(u.w < clock_thr(lat, s1, byte_at(dn, c1), m)) << c1);
+                        rR |= ((unsigned)(u.x < cthr(s0, s1)) << c0) | ((unsigned)(u.z < cthr(s1, s2)) << c1);
+                        rD |= ((unsigned)(u.y < cthr(s0, byte_at(dn, c0))) << c0) |
+                              ((unsigned)(u.w < cthr(s1, byte_at(dn, c1))) << c1);
                     }
                 }
             }
@@ -328,6 +342,25 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                     if (rv) {
                         unequal += __popc(~eqR & V) + __popc(~eqD & V);
                         pairs += 2u * (unsigned)ncols;
+                    }
+                } else if (lat.nclass <= 8) {
+                    // Up to 8 classes: 16-bit counters packed in two words per
+                    // thread, reduced over the warp once per tile.
+                    unsigned long long c_lo = 0, c_hi = 0;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        if (!(rv && c < ncols)) continue;
+                        const int s0 = byte_at(wd, c);
+                        const int s1 = (c + 1 < ncols) ? byte_at(wd, (c + 1) & 31) : (int)sr;
+                        const int d0 = clock_bond_class(s0, s1, q), d1 = clock_bond_class(s0, byte_at(dn, c), q);
+                        (d0 < 4 ? c_lo : c_hi) += 1ull << (16 * (d0 & 3));
+                        (d1 < 4 ? c_lo : c_hi) += 1ull << (16 * (d1 & 3));
+                    }
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) {
+                        const unsigned long long w = d < 4 ? c_lo : c_hi;
+                        const unsigned int v = __reduce_add_sync(FULL, (unsigned int)((w >> (16 * (d & 3))) & 0xFFFFull));
+                        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&hist_class[d], v);
                     }
                 } else {
 #pragma unroll
@@ -858,7 +891,7 @@ __device__ void finish_sweep(const Batch &b)
 // One block per tile, one warp per quadrant.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
+__global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
 {
     __shared__ __align__(16) unsigned char tab[kOpenSlots];
     __shared__ int rootg[LABELS ? kOpenSlots : 1];
@@ -868,12 +901,20 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
 
     const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
     const int qx = warp & 1, qy = warp >> 1;
-    // q <= 8: state counts of this lane, 16 bits per state (states 0-3, 4-7).
+    // q <= 8: state counts of this lane, 16 bits per state (states 0-3, 4-7);
+    // q == 2: sites in cnt_hi, sites in state 1 in cnt_lo.
     unsigned long long cnt_lo = 0, cnt_hi = 0;
     int cur = -1;
     auto flush = [&]() {
         if (MEASURE && cur >= 0) {
-            if (lat.q <= 8) {
+            if (lat.q == 2) {
+                const unsigned int n1 = __reduce_add_sync(FULL, (unsigned int)cnt_lo);
+                const unsigned int n = __reduce_add_sync(FULL, (unsigned int)cnt_hi);
+                if (r == 0) {
+                    if (n - n1) atomicAdd(&hist_state[0], n - n1);
+                    if (n1) atomicAdd(&hist_state[1], n1);
+                }
+            } else if (lat.q <= 8) {
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
                     const unsigned long long w = s < 4 ? cnt_lo : cnt_hi;
@@ -941,16 +982,15 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const uint32_t code = ((h < 2) ? (cw[k].x >> (16 * h)) : (cw[k].y >> (16 * (h - 2)))) & 0xFFFFu;
+                const int open_state = tab[code & 0xFFu];   // meaningful for open sites only
                 int ns;
-                if (code & kCodeClosed) {
-                    ns = (int)(code & 0x7Fu);
-                } else if (clock) {
+                if (clock) {
                     const int k0 = valid_state((int)((sw[k] >> (8 * h)) & 0xFFu), q);
-                    ns = tab[code] ? reflect(k0, m, q) : k0;
+                    ns = (code & kCodeClosed) ? (int)(code & 0x7Fu) : (open_state ? reflect(k0, m, q) : k0);
                 } else {
-                    ns = tab[code];
+                    ns = (code & kCodeClosed) ? (int)(code & 0x7Fu) : open_state;
                 }
-                if (MEASURE && q <= 8) {
+                if (MEASURE && q > 2 && q <= 8) {
                     const unsigned long long one = 1ull << (16 * (ns & 3));
                     if (ns < 4) cnt_lo += one;
                     else cnt_hi += one;
@@ -958,6 +998,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_flip_tiles(Batch b)
                 if (LABELS && !(code & kCodeClosed))
                     lat.label[site0 + h] = rootg[LABELS ? code : 0];
                 word |= (uint32_t)(ns & 0xFF) << (8 * h);
+            }
+            if (MEASURE && q == 2) {   // states are 0 or 1
+                cnt_lo += (unsigned)__popc(word);
+                cnt_hi += 4u;
             }
             *reinterpret_cast<uint32_t *>(lat.spin + site0) = word;
         }
