@@ -378,7 +378,7 @@ def run_ours(args, world, rank, local):
         "served": served,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": len(STAGES) * args.steps,   # one launch per stage per timed sweep
         "clocks": clocks,
         "observables": {"mean_e": obs.mean_e, "binder_u": obs.binder_u, "nmeas": int(obs.nmeas)},
     }
