@@ -121,6 +121,18 @@ def dist_setup():
     return world, rank, local
 
 
+def combine_ranks(total_ms, steps, n_sites, world, dist=None, device="cpu"):
+    """Whole-job timing of `world` independent replicas (weak scaling): the
+    slowest rank's time, its ms per step, and ns per flip over the flips of
+    all ranks."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / steps, total_ms * 1e6 / (steps * world * n_sites)
+
+
 def cpu_oracle_ns_per_flip(L, sweeps):
     """Time the CPU oracle (as it stands) on an L x L lattice: random start,
     then `sweeps` timed sweeps.  Returns (ns per flip, wall seconds)."""
@@ -268,14 +280,8 @@ def run_ours(args, world, rank, local):
         if dist is not None:
             dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, ms_per_step, value = combine_ranks(sum(step_ms), args.steps, N, world, dist, dev)
     obs = lat.measure()
-    ms_per_step = total_ms / args.steps
-    value = total_ms * 1e6 / (args.steps * world * N)
 
     # ---- per-stage device times (CUDA events around each kernel, same stream)
     prof = [0.0] * len(STAGES)
