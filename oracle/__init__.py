@@ -6,4 +6,5 @@ and Sec. 4 (clock model with embedded clusters, Eq. M^2 measurement).
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  It shares no code with the CUDA path.
 """
-from .oracle import Oracle, philox4x32_10, threshold_from_x, ncounters, observables, POTTS, CLOCK, ISING  # noqa: F401
+from .oracle import (Oracle, philox4x32_10, threshold_from_x, ncounters, observables, correlations,  # noqa: F401
+                     POTTS, CLOCK, ISING)

@@ -46,6 +46,7 @@ def _load():
     lib.swo_ncounters.restype = ctypes.c_int
     lib.swo_sweep.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p]
     lib.swo_counts.argtypes = [ctypes.c_void_p, c_i64p]
+    lib.swo_correlations.argtypes = [ctypes.c_int, ctypes.c_int, c_i64p, ctypes.POINTER(ctypes.c_double)]
     lib.swo_observables.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_i64p,
                                     ctypes.POINTER(ctypes.c_double)]
     lib.swo_sample_one_step.argtypes = [ctypes.c_void_p, c_i8p, ctypes.c_uint64, ctypes.c_int, c_i8p]
@@ -92,6 +93,20 @@ def observables(L, q, model, counts):
         lib.swo_observables(int(L), int(q), int(model), _ptr(row, ctypes.c_int64), _ptr(o, ctypes.c_double))
         out[r] = o
     return out
+
+
+def correlations(L, q, counts):
+    """Clock model: {G(L/4), G(L/2)} from one counter row (or an array of rows)."""
+    lib = _load()
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    rows = c[None, :] if c.ndim == 1 else c
+    out = np.zeros((rows.shape[0], 2), dtype=np.float64)
+    for r in range(rows.shape[0]):
+        row = np.ascontiguousarray(rows[r])
+        o = np.zeros(2, dtype=np.float64)
+        lib.swo_correlations(int(L), int(q), _ptr(row, ctypes.c_int64), _ptr(o, ctypes.c_double))
+        out[r] = o
+    return out[0] if c.ndim == 1 else out
 
 
 class Oracle:

@@ -205,7 +205,8 @@ int swo_last_axis(const swo *o) { return o->axis; }
 int swo_ncounters(int q, int model)
 {
     int nclass = (model == SWO_CLOCK) ? q / 2 + 1 : 2;
-    return q + nclass + 2;
+    /* clock: two more class histograms, pairs at distance L/4 and L/2 */
+    return q + nclass + 2 + (model == SWO_CLOCK ? 2 * nclass : 0);
 }
 
 static int64_t right_of(const swo *o, int64_t i)
@@ -346,6 +347,25 @@ void swo_counts(const swo *o, int64_t *c)
     }
     c[q + nclass] = o->active;
     c[q + nclass + 1] = o->clusters;
+    if (o->model == SWO_CLOCK) {
+        /* Correlation at distance r = L/4 and L/2 (Sec. 4, G(r,T)): the class
+         * min(dk, q - dk) of every pair (i, i + r x) and (i, i + r y). */
+        int64_t L = o->L;
+        for (int w = 0; w < 2; ++w) {
+            int64_t r = (w == 0) ? L / 4 : L / 2;
+            int64_t *h = c + q + nclass + 2 + (int64_t)w * nclass;
+            for (int64_t y = 0; y < L; ++y) {
+                for (int64_t x = 0; x < L; ++x) {
+                    int a = o->spin[y * L + x];
+                    int bx = o->spin[y * L + (x + r) % L];
+                    int by = o->spin[((y + r) % L) * L + x];
+                    int dx = ((a - bx) % q + q) % q, dy = ((a - by) % q + q) % q;
+                    h[dx < q - dx ? dx : q - dx]++;
+                    h[dy < q - dy ? dy : q - dy]++;
+                }
+            }
+        }
+    }
 }
 
 void swo_sweep(swo *o, int n, int64_t *counts)
@@ -394,6 +414,21 @@ void swo_observables(int L, int q, int model, const int64_t *c, double *out)
     out[1] = sqrt(M2) / dN;
     out[2] = m2;
     out[3] = m2 * m2;
+}
+
+/* Clock model: G(L/4) and G(L/2) of one counter row, the mean of
+ * cos(theta_i - theta_{i+r}) over the 2N pairs of each distance (x and y
+ * displacements): sum_d class_d cos(2 pi d / q) / (2N). */
+void swo_correlations(int L, int q, const int64_t *c, double *out)
+{
+    int nclass = q / 2 + 1;
+    double pairs = 2.0 * (double)L * (double)L;
+    for (int w = 0; w < 2; ++w) {
+        const int64_t *h = c + q + nclass + 2 + (int64_t)w * nclass;
+        double g = 0.0;
+        for (int d = 0; d < nclass; ++d) g += (double)h[d] * cos(2.0 * M_PI * (double)d / (double)q);
+        out[w] = g / pairs;
+    }
 }
 
 void swo_label_bonds(swo *o, const uint8_t *bonds, int64_t nsets, int32_t *labels)

@@ -70,7 +70,8 @@ uint64_t swo_get_sweep(const swo *o);
 void swo_set_sweep(swo *o, uint64_t t);
 int swo_last_axis(const swo *o);
 
-/* Number of int64 counters per measurement: q + nclass + 2. */
+/* Number of int64 counters per measurement: q + nclass + 2, and for the
+ * clock model 2 * nclass more. */
 int swo_ncounters(int q, int model);
 
 /* Run n sweeps.  If counts != NULL, write the counters measured after
@@ -79,7 +80,10 @@ int swo_ncounters(int q, int model);
  *   [class_0 .. class_{nc-1}] bond classes of the new configuration
  *       (Potts/Ising: nc = 2, class 0 = equal pair, class 1 = unequal;
  *        clock: nc = q/2 + 1, class d counts bonds with min(dk, q-dk) = d),
- *   [active] active bonds of the sweep, [clusters] clusters of the sweep. */
+ *   [active] active bonds of the sweep, [clusters] clusters of the sweep,
+ *   clock only: [corr4_0 .. corr4_{nc-1}] [corr2_0 .. corr2_{nc-1}], the
+ *       classes of the 2N pairs (i, i + r x), (i, i + r y) at r = L/4 and
+ *       r = L/2 (Sec. 4, G(r,T)). */
 void swo_sweep(swo *o, int n, int64_t *counts);
 
 /* Counters of the current configuration (active/clusters of the last sweep). */
@@ -87,6 +91,9 @@ void swo_counts(const swo *o, int64_t *counts);
 
 /* FP64 observables from one counter row: out = {E/N, |m|, m^2, m^4}. */
 void swo_observables(int L, int q, int model, const int64_t *counts, double *out);
+
+/* Clock model: out = {G(L/4), G(L/2)} from one counter row (Sec. 4). */
+void swo_correlations(int L, int q, const int64_t *counts, double *out);
 
 /* Label nsets given bond configurations (N bytes each, bit0 right, bit1
  * down) with the same search the sweep uses; labels: nsets x N. */

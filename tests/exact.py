@@ -49,6 +49,21 @@ def ising_exact(L, T):
             "m2": float(w @ m ** 2), "m4": float(w @ m ** 4)}
 
 
+def ising_correlation_exact(L, T, r):
+    """Exact <s_i s_{i+r}> of the Ising torus (H = -sum s_i s_j), averaged over
+    every site and both lattice directions."""
+    N = L * L
+    s = 1 - 2 * all_states(N, 2).astype(np.int64)
+    b = torus_bonds(L)
+    E = -(s[:, b[:, 0]] * s[:, b[:, 1]]).sum(axis=1).astype(np.float64)
+    idx = np.arange(N).reshape(L, L)
+    px = np.roll(idx, -r, axis=1).reshape(-1)   # site (y, x + r)
+    py = np.roll(idx, -r, axis=0).reshape(-1)   # site (y + r, x)
+    c = ((s * s[:, px]).sum(axis=1) + (s * s[:, py]).sum(axis=1)) / (2.0 * N)
+    w = _boltzmann(E, 1.0 / T)
+    return float(w @ c)
+
+
 def potts_exact(L, q, T):
     """Exact <E/N>, <m^2> of the q-state Potts torus, Eq. (1): E = #unequal pairs,
     m^2 = M^2/N^2 with M^2 from Eq. (M^2)."""

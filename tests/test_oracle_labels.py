@@ -41,7 +41,8 @@ def test_labels_match_scipy_components(L, model, q, T):
         want, nc = scipy_labels(L, o.bonds.reshape(-1))
         lab = o.labels.reshape(-1)
         assert np.array_equal(lab, want)
-        assert o.counts()[-1] == nc
+        nclass = q // 2 + 1 if model == CLOCK else 2
+        assert o.counts()[q + nclass + 1] == nc   # clusters
         assert np.all(lab <= np.arange(L * L))
         assert np.array_equal(lab[lab], lab)
 

@@ -86,7 +86,8 @@ def test_no_bonds_every_site_draws_its_own_state(table, model, q):
     want = _mulhi(table[(3, TAG_STATE)][: L * L, 0], q)
     assert np.array_equal(o.spins.reshape(-1), want)
     assert np.array_equal(o.labels.reshape(-1), np.arange(L * L))
-    assert rec[-2] == 0 and rec[-1] == L * L
+    nclass = q // 2 + 1 if model == CLOCK else 2
+    assert rec[q + nclass] == 0 and rec[q + nclass + 1] == L * L   # active bonds, clusters
     assert o.sweep_index == 4
 
 
@@ -123,8 +124,8 @@ def test_bond_lanes_labels_and_root_draws(table, L):
     want_spins = _mulhi(table[(0, TAG_STATE)][want_labels, 0], q)
     assert np.array_equal(o.spins.reshape(-1), want_spins)
     rec = o.counts()
-    assert rec[-2] == right.sum() + down.sum()
-    assert rec[-1] == nc
+    assert rec[q + 2] == right.sum() + down.sum()   # active bonds (Potts: 2 classes)
+    assert rec[q + 3] == nc                          # clusters
 
 
 def test_clock_axis_and_single_site_reflections(table):
