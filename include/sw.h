@@ -41,6 +41,9 @@
  *                      clock: C = q/2 + 1, class d = min(dk, q - dk)
  *   active             active bonds of the sweep
  *   clusters           clusters of the sweep
+ *   clock only: corr4_0 .. corr4_{C-1}, corr2_0 .. corr2_{C-1}: the classes
+ *                      d of the 2N pairs (i, i + r x), (i, i + r y) at
+ *                      r = L/4 and r = L/2 (Sec. 4, correlation G(r,T))
  *
  * Errors: every int-returning call returns SW_OK (0) or a negative status;
  * sw_last_error() gives a thread-local message.  The library never exits or
@@ -94,9 +97,13 @@ typedef struct sw_obs {
     double mean_e, mean_e2, mean_absm, mean_m2, mean_m4;
     double binder_u;             /* mean_m4 / mean_m2^2 (Eq. U)              */
     double mean_active, mean_clusters;
+    /* clock model (0 otherwise): G(r) = <cos(theta_i - theta_{i+r})> over the
+     * pairs at r = L/4 and L/2 (Sec. 4), last sweep and running means, and
+     * R = mean G(L/2) / mean G(L/4) (Sec. 4, R(T)) */
+    double g_quarter, g_half, mean_g_quarter, mean_g_half, corr_ratio;
 } sw_obs;
 
-/* Number of counters per sweep for (q, model): q + C + 2. */
+/* Number of counters per sweep for (q, model): q + C + 2 (clock: q + 3C + 2). */
 int sw_ncounters(int q, int model);
 
 /* Create a lattice on the current device: 4 <= L <= 46340, L % 4 == 0;

@@ -42,6 +42,8 @@ class sw_obs(ctypes.Structure):
         ("mean_m2", ctypes.c_double), ("mean_m4", ctypes.c_double),
         ("binder_u", ctypes.c_double),
         ("mean_active", ctypes.c_double), ("mean_clusters", ctypes.c_double),
+        ("g_quarter", ctypes.c_double), ("g_half", ctypes.c_double), ("mean_g_quarter", ctypes.c_double),
+        ("mean_g_half", ctypes.c_double), ("corr_ratio", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -62,6 +62,10 @@ uint32_t threshold_of(double x)
 
 int nclass_of(int q, int model) { return model == SW_CLOCK ? q / 2 + 1 : 2; }
 
+// Counters per sweep: n_k, bond classes, active bonds, clusters; the clock
+// model adds the class histograms of the pairs at distance L/4 and L/2.
+int ncounters_of(int q, int model) { return q + nclass_of(q, model) + 2 + (model == SW_CLOCK ? 2 * nclass_of(q, model) : 0); }
+
 }  // namespace
 
 struct sw_handle {
@@ -102,6 +106,7 @@ struct sw_handle {
     bool have_last = false;
     uint64_t nmeas = 0;
     double sum_e = 0, sum_e2 = 0, sum_absm = 0, sum_m2 = 0, sum_m4 = 0, sum_active = 0, sum_clusters = 0;
+    double sum_g4 = 0, sum_g2 = 0;   // clock: correlation at L/4 and L/2
     // captured sweep
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -231,6 +236,20 @@ void observables_of(int L, int q, int model, const int64_t *c, double out[4])
     out[3] = m2 * m2;
 }
 
+// Clock model, Sec. 4: G(r) = <cos(theta_i - theta_{i+r})> over the 2N pairs
+// at r = L/4 and r = L/2 (x and y displacements), from their class counts.
+void correlations_of(int L, int q, const int64_t *c, double g[2])
+{
+    const int nclass = q / 2 + 1;
+    const double pairs = 2.0 * (double)L * (double)L;
+    for (int w = 0; w < 2; ++w) {
+        const int64_t *hst = c + q + nclass + 2 + w * nclass;
+        double s = 0.0;
+        for (int d = 0; d < nclass; ++d) s += (double)hst[d] * std::cos(2.0 * M_PI * (double)d / (double)q);
+        g[w] = s / pairs;
+    }
+}
+
 void accumulate(sw_handle *h, const int64_t *row)
 {
     double o[4];
@@ -243,6 +262,12 @@ void accumulate(sw_handle *h, const int64_t *row)
     h->sum_m4 += o[3];
     h->sum_active += (double)row[h->q + h->nclass];
     h->sum_clusters += (double)row[h->q + h->nclass + 1];
+    if (h->model == SW_CLOCK) {
+        double g[2];
+        correlations_of(h->L, h->q, row, g);
+        h->sum_g4 += g[0];
+        h->sum_g2 += g[1];
+    }
     h->last_counts.assign(row, row + h->ncounters);
     h->have_last = true;
     if (h->record) h->history.insert(h->history.end(), row, row + h->ncounters);
@@ -473,7 +498,7 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
     h->T = T;
     h->seed = seed;
     h->nclass = nclass_of(q, model);
-    h->ncounters = q + h->nclass + 2;
+    h->ncounters = ncounters_of(q, model);
     const size_t N = (size_t)L * L;
     auto bail = [&](cudaError_t e, const char *what) -> sw_handle * {
         cuda_fail(e, what);
@@ -578,7 +603,7 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
 
 extern "C" {
 
-int sw_ncounters(int q, int model) { return q + nclass_of(q, model) + 2; }
+int sw_ncounters(int q, int model) { return ncounters_of(q, model); }
 
 const char *sw_last_error(void) { return g_err.c_str(); }
 
@@ -655,6 +680,12 @@ int sw_measure(sw_handle *h, sw_obs *out)
         out->absm = o[1];
         out->m2 = o[2];
         out->m4 = o[3];
+        if (h->model == SW_CLOCK) {
+            double g[2];
+            correlations_of(h->L, h->q, h->last_counts.data(), g);
+            out->g_quarter = g[0];
+            out->g_half = g[1];
+        }
     }
     out->nmeas = h->nmeas;
     if (h->nmeas) {
@@ -667,6 +698,11 @@ int sw_measure(sw_handle *h, sw_obs *out)
         out->binder_u = out->mean_m2 > 0 ? out->mean_m4 / (out->mean_m2 * out->mean_m2) : 0.0;
         out->mean_active = h->sum_active / n;
         out->mean_clusters = h->sum_clusters / n;
+        if (h->model == SW_CLOCK) {
+            out->mean_g_quarter = h->sum_g4 / n;
+            out->mean_g_half = h->sum_g2 / n;
+            out->corr_ratio = out->mean_g_quarter != 0.0 ? out->mean_g_half / out->mean_g_quarter : 0.0;
+        }
     }
     return SW_OK;
 }
@@ -712,6 +748,7 @@ int sw_reset_stats(sw_handle *h)
     if (rc != SW_OK) return rc;
     h->nmeas = 0;
     h->sum_e = h->sum_e2 = h->sum_absm = h->sum_m2 = h->sum_m4 = h->sum_active = h->sum_clusters = 0.0;
+    h->sum_g4 = h->sum_g2 = 0.0;
     return SW_OK;
 }
 
@@ -1307,7 +1344,7 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     if (rc != SW_OK) return rc;
     const cudaStream_t s = (cudaStream_t)stream;
     const bool measure = d_counts != nullptr;
-    const int nclass = nclass_of(q, model), nc = q + nclass + 2;
+    const int nclass = nclass_of(q, model), nc = ncounters_of(q, model);
     const int tiles_x = (L + swgb::kTileW - 1) / swgb::kTileW, tiles_y = (L + swgb::kTileH - 1) / swgb::kTileH;
 
     Lattice lat{};

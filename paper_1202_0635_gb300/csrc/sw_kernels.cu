@@ -182,6 +182,64 @@ __global__ void k_init(Lattice lat, int random)
     }
 }
 
+// The states at distance r to the right (px) and below (py) of the half
+// row (y, x0 .. x0 + ncols - 1), four to a word like the row itself.
+__device__ __forceinline__ void load_partners(const int8_t *spin, int L, int y, int x0, int r, int ncols, bool rv,
+                                              uint32_t (&px)[8], uint32_t (&py)[8])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) px[k] = py[k] = 0u;
+    if (!rv) return;
+    const int yr = (y + r) % L;
+    const uint32_t *prow = reinterpret_cast<const uint32_t *>(spin + (size_t)yr * L + x0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) py[k] = (4 * k < ncols) ? __ldg(prow + k) : 0u;
+    const int cx = (x0 + r) % L;
+    if ((cx & 3) == 0 && cx + ncols <= L) {   // word aligned, no wrap
+        const uint32_t *xrow = reinterpret_cast<const uint32_t *>(spin + (size_t)y * L + cx);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) px[k] = (4 * k < ncols) ? __ldg(xrow + k) : 0u;
+    } else {
+        for (int j = 0; j < ncols; ++j) {
+            const uint32_t b = (uint8_t)__ldg(spin + (size_t)y * L + (x0 + j + r) % L);
+            px[j >> 2] |= b << (8 * (j & 3));
+        }
+    }
+}
+
+// Clock classes min(dk, q - dk) of the pairs (row byte c, px byte c) and
+// (row byte c, py byte c), c < ncols, into a shared histogram.  Must be
+// called by all 32 lanes of the warp.
+__device__ __forceinline__ void count_pair_classes(unsigned int *hist, const uint32_t (&wd)[8], const uint32_t (&px)[8],
+                                                   const uint32_t (&py)[8], int ncols, bool rv, int q, int nclass)
+{
+    if (nclass <= 8) {
+        unsigned long long c_lo = 0, c_hi = 0;   // 16-bit counters, classes 0-3 and 4-7
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            if (!(rv && c < ncols)) continue;
+            const int s0 = byte_at(wd, c);
+            const int d0 = clock_bond_class(s0, byte_at(px, c), q), d1 = clock_bond_class(s0, byte_at(py, c), q);
+            (d0 < 4 ? c_lo : c_hi) += 1ull << (16 * (d0 & 3));
+            (d1 < 4 ? c_lo : c_hi) += 1ull << (16 * (d1 & 3));
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const unsigned long long w = d < 4 ? c_lo : c_hi;
+            const unsigned int v = __reduce_add_sync(FULL, (unsigned int)((w >> (16 * (d & 3))) & 0xFFFFull));
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(&hist[d], v);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const bool v = rv && c < ncols;
+            const int s0 = byte_at(wd, c);
+            add_hist_any(hist, clock_bond_class(s0, byte_at(px, c), q), v);
+            add_hist_any(hist, clock_bond_class(s0, byte_at(py, c), q), v);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_bonds: the bonds of every site (Sec. 2 step (ii); clock: Sec. 4).
 // Thread = one 32-site half row of a tile: equal-neighbour masks from packed
@@ -201,6 +259,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
     __shared__ uint32_t s_thr[SW_MAX_CLOCK_Q * SW_MAX_CLOCK_Q];
     __shared__ uint8_t s_proj[SW_MAX_CLOCK_Q];
     __shared__ unsigned int hist_class[SW_MAX_CLOCK_Q / 2 + 2];
+    __shared__ unsigned int hist_corr[2][SW_MAX_CLOCK_Q / 2 + 2];   // clock: pairs at L/4, L/2
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
@@ -218,8 +277,13 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                     block_add<kBlockThreads>(prev + lat.q + 0, pairs - unequal, red);
                 } else {
                     __syncthreads();
-                    for (int k = threadIdx.x; k < lat.nclass; k += blockDim.x)
+                    const int nc = lat.nclass;
+                    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
                         if (hist_class[k]) atomicAdd(prev + lat.q + k, (unsigned long long)hist_class[k]);
+                        for (int w = 0; w < 2; ++w)
+                            if (hist_corr[w][k])
+                                atomicAdd(prev + lat.q + nc + 2 + w * nc + k, (unsigned long long)hist_corr[w][k]);
+                    }
                 }
             }
         }
@@ -235,7 +299,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
             __syncthreads();
             if (threadIdx.x == 0) ctx = task_context<MEASURE>(lat);
             if (MEASURE)
-                for (int k = threadIdx.x; k < SW_MAX_CLOCK_Q / 2 + 2; k += blockDim.x) hist_class[k] = 0u;
+                for (int k = threadIdx.x; k < SW_MAX_CLOCK_Q / 2 + 2; k += blockDim.x)
+                    hist_class[k] = hist_corr[0][k] = hist_corr[1][k] = 0u;
             __syncthreads();
             if (lat.clock) {
                 const int q = lat.q;
@@ -370,6 +435,17 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                         const int s1 = (c + 1 < ncols) ? byte_at(wd, (c + 1) & 31) : (int)sr;
                         add_hist_any(hist_class, clock_bond_class(s0, s1, q), v);
                         add_hist_any(hist_class, clock_bond_class(s0, byte_at(dn, c), q), v);
+                    }
+                }
+                if (clock) {
+                    // Correlation pairs (i, i + r x), (i, i + r y) at r = L/4 and
+                    // r = L/2 (Sec. 4, G(r,T)) of the incoming configuration.
+#pragma unroll 1
+                    for (int w = 0; w < 2; ++w) {
+                        const int r = w == 0 ? L / 4 : L / 2;
+                        uint32_t px[8], py[8];
+                        load_partners(lat.spin, L, y, x0, r, ncols, rv, px, py);
+                        count_pair_classes(hist_corr[w], wd, px, py, ncols, rv, q, lat.nclass);
                     }
                 }
             }
@@ -1032,12 +1108,13 @@ template <bool CLOCK>
 __global__ void __launch_bounds__(kEnergyThreads) k_pending_classes(Lattice lat)
 {
     __shared__ unsigned int hist[SW_MAX_CLOCK_Q / 2 + 2];
+    __shared__ unsigned int hist_corr[2][SW_MAX_CLOCK_Q / 2 + 2];   // clock: pairs at L/4, L/2
     __shared__ unsigned int red[32];
     const unsigned long long t = read_u64(&lat.st->sweep);
     if (t == 0ull || t - 1ull < read_u64(&lat.st->classes_upto)) return;   // same for every block
     const int L = lat.L, q = lat.q;
     if (CLOCK)
-        for (int k = threadIdx.x; k < lat.nclass; k += blockDim.x) hist[k] = 0u;
+        for (int k = threadIdx.x; k < lat.nclass; k += blockDim.x) hist[k] = hist_corr[0][k] = hist_corr[1][k] = 0u;
     __syncthreads();
     const long long N4 = (long long)L * L / 4;
     unsigned int unequal = 0, sites = 0;
@@ -1066,6 +1143,21 @@ __global__ void __launch_bounds__(kEnergyThreads) k_pending_classes(Lattice lat)
         if (CLOCK) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) add_hist_any(hist, clock_bond_class(a[k], bb[k], q), v);
+            // Correlation pairs at r = L/4 and L/2 (Sec. 4, G(r,T)).
+            const int i0 = v ? (int)(4 * g) : 0;
+            const int y = i0 / L, x = i0 - y * L;
+#pragma unroll 1
+            for (int w = 0; w < 2; ++w) {
+                const int r = w == 0 ? L / 4 : L / 2;
+                const size_t yrow = (size_t)((y + r) % L) * L;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int sx = v ? lat.spin[(size_t)y * L + (x + k + r) % L] : 0;
+                    const int sy = v ? lat.spin[yrow + x + k] : 0;
+                    add_hist_any(hist_corr[w], clock_bond_class(a[k], sx, q), v);
+                    add_hist_any(hist_corr[w], clock_bond_class(a[k], sy, q), v);
+                }
+            }
         } else if (v) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) unequal += (a[k] != bb[k]);
@@ -1074,8 +1166,12 @@ __global__ void __launch_bounds__(kEnergyThreads) k_pending_classes(Lattice lat)
     unsigned long long *row = ring_row(lat, t - 1);
     if (CLOCK) {
         __syncthreads();
-        for (int k = threadIdx.x; k < lat.nclass; k += blockDim.x)
+        const int nc = lat.nclass;
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) {
             if (hist[k]) atomicAdd(row + q + k, (unsigned long long)hist[k]);
+            for (int w = 0; w < 2; ++w)
+                if (hist_corr[w][k]) atomicAdd(row + q + nc + 2 + w * nc + k, (unsigned long long)hist_corr[w][k]);
+        }
     } else {
         block_add<kEnergyThreads>(row + q + 1, unequal, red);
         block_add<kEnergyThreads>(row + q + 0, 2u * sites - unequal, red);

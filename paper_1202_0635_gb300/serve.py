@@ -34,7 +34,7 @@ def job_bytes(L, q, model):
     n = L * L
     tiles = ((L + 63) // 64) ** 2
     nclass = q // 2 + 1 if model == 1 else 2
-    ring = 1024 * (q + nclass + 2) * 8
+    ring = 1024 * (q + nclass + 2 + (2 * nclass if model == 1 else 0)) * 8
     table = (2 * q) ** 2 * 4 if model == 1 else 0
     return n * (1 + 2 + 4) + tiles * (1024 + 256 * 5 + 4 + 16) + ring + table + 4096
 

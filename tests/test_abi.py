@@ -45,7 +45,7 @@ def test_binding_covers_every_declared_symbol():
 def test_host_only_entry_points(lib):
     import paper_1202_0635_gb300 as sw
     assert sw.sw_ncounters(2, sw.SW_ISING) == 6
-    assert sw.sw_ncounters(6, sw.SW_CLOCK) == 6 + 4 + 2
+    assert sw.sw_ncounters(6, sw.SW_CLOCK) == 6 + 3 * 4 + 2   # + correlation classes at L/4, L/2
     assert sw.sw_ncounters(3, sw.SW_POTTS) == 3 + 2 + 2
     assert lib.sw_destroy(None) == 0
     assert lib.sw_sweep(None, 1) == sw.SW_ERR_ARG

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import paper_1202_0635_gb300 as sw
-from oracle import CLOCK, ISING, POTTS, Oracle, observables
+from oracle import CLOCK, ISING, POTTS, Oracle, correlations, observables
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +67,14 @@ def run_lockstep(L, q, model, T, seed, init, n, graph=False, labels=True, every=
             want += v
         want /= n
         assert abs(getattr(obs, name) - want) <= 1e-12 * max(1.0, abs(want)), name
+    if model == CLOCK:   # correlations at L/4 and L/2 (Sec. 4) and their ratio R
+        gref = correlations(L, q, rows)
+        want4, want2 = gref[:, 0].mean(), gref[:, 1].mean()
+        assert abs(obs.mean_g_quarter - want4) <= 1e-12 * max(1.0, abs(want4))
+        assert abs(obs.mean_g_half - want2) <= 1e-12 * max(1.0, abs(want2))
+        if want4 != 0.0:
+            assert abs(obs.corr_ratio - want2 / want4) <= 1e-9 * max(1.0, abs(want2 / want4))
+        assert np.allclose([obs.g_quarter, obs.g_half], gref[-1], rtol=1e-12, atol=1e-15)
     g.close()
     return rows
 
@@ -83,7 +91,8 @@ def test_potts_critical(L, q):
 
 
 @pytest.mark.parametrize("L", [8, 36, 96, 128])
-@pytest.mark.parametrize("q,T", [(6, 0.7), (6, 0.9), (6, 1.2), (4, 0.8), (5, 0.9), (3, 0.6), (8, 0.5)])
+@pytest.mark.parametrize("q,T", [(6, 0.7), (6, 0.9), (6, 1.2), (4, 0.8), (5, 0.9), (3, 0.6), (8, 0.5),
+                                 (16, 0.3), (64, 0.2)])
 def test_clock(L, q, T):
     run_lockstep(L, q, CLOCK, T, 99, "random", 25)
 
