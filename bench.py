@@ -173,6 +173,29 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_large(sw, torch, dev, sizes=(8192, 16384, 46340), sweeps=10):
+    """Single lattices beyond the benchmark size, up to the int32 label limit
+    (L = 46340, 2.1e9 sites): q=2 Potts at T_c, random start, CUDA graph,
+    measurement on; inputs exceed the L2, so no flush."""
+    out = []
+    for L in sizes:
+        stream = torch.cuda.Stream(device=dev)
+        lat = sw.Lattice(L, Q_BENCH, sw.SW_POTTS, T_BENCH, 1, init=sw.SW_INIT_RANDOM, stream=stream.cuda_stream)
+        sw.sw_set_graph(lat.h, 1)
+        lat.sweep(sweeps)
+        sw.sw_synchronize(lat.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.sweep(sweeps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / sweeps
+        sw.sw_synchronize(lat.h)
+        lat.close()
+        out.append({"L": L, "ms_per_sweep": ms, "ns_per_flip": ms * 1e6 / (L * L)})
+    return out
+
+
 def run_batched(sw, torch, dev, steps):
     """256 independent replicas of uneven L, model and T (seeded recipe) in one
     batched launch sequence per sweep, against a loop of plain per-replica
@@ -349,6 +372,9 @@ def run_ours(args, world, rank, local):
     batched = None
     if not args.no_batched:
         batched = run_batched(sw, torch, dev, args.steps)
+    large = None
+    if not args.no_large and world == 1:
+        large = run_large(sw, torch, dev)
     served = None
     if not args.no_served and world == 1:
         served = run_served()
@@ -381,6 +407,7 @@ def run_ours(args, world, rank, local):
         "stage_us": stage_us,
         "update_only_ns_per_flip": update_only,
         "batched": batched,
+        "large_lattices": large,
         "served": served,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N, "d2h_bytes_per_step": d2h},
@@ -400,6 +427,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

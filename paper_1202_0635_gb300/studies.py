@@ -1,0 +1,119 @@
+"""Temperature scans on the GPU engine (Komura & Okabe, arXiv:1202.0635,
+Sec. 4): the moment ratio U(T) = <M^4>/<M^2>^2 of several sizes (Eq. U; the
+crossing of the curves marks the critical point, Fig. 3), the time per spin
+flip against T with its per-stage split (Figs. 2 and 5), and the
+correlation ratio R(T) = G(L/2)/G(L/4) of the clock model (Fig. 6).
+
+Every (L, T) point is its own lattice; all of them advance together in one
+batch (one launch sequence per sweep), so a scan costs about as much as
+its largest lattice.
+
+    python -m paper_1202_0635_gb300.studies --q 2 --L 32 64 128 --sweeps 4000
+"""
+import argparse
+import importlib
+import json
+import math
+
+from . import workloads
+
+
+def _sw():
+    return importlib.import_module(__package__)
+
+
+def temperatures(q, model, lo=0.9, hi=1.1, n=9):
+    """n temperatures evenly spaced in [lo, hi] * T_c."""
+    tc = workloads.critical_temperature(q, model)
+    return [tc * (lo + (hi - lo) * k / (n - 1)) for k in range(n)]
+
+
+def scan(q, model, sizes, temps, sweeps, equil=200, seed=1):
+    """Running means of every (L, T) lattice after `equil` discarded sweeps
+    and `sweeps` measured ones: list of dicts (L, T, e, m2, m4, U, clusters,
+    and for the clock model G(L/4), G(L/2), R)."""
+    sw = _sw()
+    b = sw.Batch()
+    try:
+        points = []
+        for i, L in enumerate(sizes):
+            for j, T in enumerate(temps):
+                lat = b.add(L, q, model, T, seed + 1000 * i + j, init=sw.SW_INIT_RANDOM)
+                points.append((L, T, lat))
+        sw.sw_batch_set_graph(b.b, 1)
+        b.sweep(equil)
+        for _, _, lat in points:
+            sw.sw_reset_stats(lat.h)
+        b.sweep(sweeps)
+        out = []
+        for L, T, lat in points:
+            o = lat.measure()
+            row = {"L": L, "T": T, "sweeps": int(o.nmeas), "e": o.mean_e, "m2": o.mean_m2, "m4": o.mean_m4,
+                   "U": o.binder_u, "clusters": o.mean_clusters}
+            if model == sw.SW_CLOCK:
+                row.update({"g_quarter": o.mean_g_quarter, "g_half": o.mean_g_half, "R": o.corr_ratio})
+            out.append(row)
+        return out
+    finally:
+        b.close()
+
+
+def crossing(rows, key, small, large):
+    """Temperature where key(T) of two sizes cross, by linear interpolation
+    between the scanned temperatures that bracket the sign change of
+    key(large) - key(small); None if the curves do not cross."""
+    a = sorted((r["T"], r[key]) for r in rows if r["L"] == small)
+    c = sorted((r["T"], r[key]) for r in rows if r["L"] == large)
+    diff = [(ta, vc - va) for (ta, va), (tc, vc) in zip(a, c)]
+    for (t0, d0), (t1, d1) in zip(diff, diff[1:]):
+        if d0 == 0.0:
+            return t0
+        if d0 * d1 < 0.0:
+            return t0 + (t1 - t0) * d0 / (d0 - d1)
+    return None
+
+
+def timing(q, model, L, temps, sweeps=20, equil=50, seed=1):
+    """Per-stage device time per spin flip (ns) of one lattice at each T,
+    CUDA events around every kernel of direct-launched sweeps."""
+    sw = _sw()
+    stages = ["bonds", "label", "merge", "flatten", "flip"]
+    out = []
+    for T in temps:
+        lat = sw.Lattice(L, q, model, T, seed, init=sw.SW_INIT_RANDOM)
+        try:
+            lat.sweep(equil)
+            ms = sw.sw_profile_sweeps(lat.h, sweeps)
+        finally:
+            lat.close()
+        per = {name: ms[k] * 1e6 / (L * L) for k, name in enumerate(stages)}
+        out.append({"T": T, "ns_per_flip": sum(per.values()), "stages_ns_per_flip": per})
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--q", type=int, default=2)
+    ap.add_argument("--model", choices=["potts", "clock"], default="potts")
+    ap.add_argument("--L", type=int, nargs="+", default=[32, 64, 128])
+    ap.add_argument("--sweeps", type=int, default=4000)
+    ap.add_argument("--equil", type=int, default=500)
+    ap.add_argument("--lo", type=float, default=0.9)
+    ap.add_argument("--hi", type=float, default=1.1)
+    ap.add_argument("--n", type=int, default=9)
+    ap.add_argument("--timing-L", type=int, default=1024)
+    args = ap.parse_args()
+    sw = _sw()
+    sw.lib()
+    model = sw.SW_CLOCK if args.model == "clock" else sw.SW_POTTS
+    temps = temperatures(args.q, model, args.lo, args.hi, args.n)
+    rows = scan(args.q, model, args.L, temps, args.sweeps, args.equil)
+    key = "R" if model == sw.SW_CLOCK else "U"
+    cross = {"%d-%d" % (a, c): crossing(rows, key, a, c) for a, c in zip(args.L, args.L[1:])}
+    print(json.dumps({"q": args.q, "model": args.model, "T_c": workloads.critical_temperature(args.q, model),
+                      "points": rows, "crossings_" + key: cross,
+                      "timing_L%d" % args.timing_L: timing(args.q, model, args.timing_L, temps)}))
+
+
+if __name__ == "__main__":
+    main()
