@@ -196,6 +196,33 @@ def run_large(sw, torch, dev, sizes=(8192, 16384, 46340), sweeps=10):
     return out
 
 
+def run_comparators(sw, torch, dev, L=L_BENCH, sweeps=10, equil=20):
+    """The paper's own labelings (Sec. 3: Hawick et al., Kalentev et al.) on
+    this GPU, same workload, update only (the paper's "update only" rows):
+    ns per flip per sweep (host reads the convergence flag after every pass,
+    as in the paper) and the mean number of scan passes."""
+    out = {}
+    for name, method in (("hawick", sw.SW_LABEL_HAWICK), ("kalentev", sw.SW_LABEL_KALENTEV)):
+        stream = torch.cuda.Stream(device=dev)
+        lat = sw.Lattice(L, Q_BENCH, sw.SW_POTTS, T_BENCH, 1, init=sw.SW_INIT_RANDOM, stream=stream.cuda_stream)
+        sw.sw_set_measure(lat.h, 0)
+        sw.sw_set_labeling(lat.h, method)
+        lat.sweep(equil)
+        sw.sw_synchronize(lat.h)
+        passes = 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(sweeps):
+            lat.sweep(1)
+            passes += sw.sw_label_passes(lat.h)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / sweeps
+        lat.close()
+        out[name] = {"L": L, "ms_per_sweep": ms, "ns_per_flip": ms * 1e6 / (L * L), "mean_passes": passes / sweeps}
+    return out
+
+
 def run_batched(sw, torch, dev, steps):
     """256 independent replicas of uneven L, model and T (seeded recipe) in one
     batched launch sequence per sweep, against a loop of plain per-replica
@@ -375,6 +402,9 @@ def run_ours(args, world, rank, local):
     large = None
     if not args.no_large and world == 1:
         large = run_large(sw, torch, dev)
+    comparators = None
+    if not args.no_comparators and world == 1:
+        comparators = run_comparators(sw, torch, dev)
     served = None
     if not args.no_served and world == 1:
         served = run_served()
@@ -408,6 +438,7 @@ def run_ours(args, world, rank, local):
         "update_only_ns_per_flip": update_only,
         "batched": batched,
         "large_lattices": large,
+        "paper_labelings_update_only": comparators,
         "served": served,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N, "d2h_bytes_per_step": d2h},
@@ -428,6 +459,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

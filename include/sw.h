@@ -188,6 +188,22 @@ int sw_set_sweep(sw_handle *h, uint64_t t);
 int sw_autotune(sw_handle *h, int n, int *shape_out);
 int sw_set_launch_shape(sw_handle *h, const int *shape);
 
+/* Cluster labeling of the handle's sweeps.  SW_LABEL_TILED (default) is the
+ * library's tile-local labeling plus a boundary merge.  SW_LABEL_HAWICK and
+ * SW_LABEL_KALENTEV are the paper's GPU labelings (Sec. 3: Hawick et al.'s
+ * label equivalence with a reference array and atomicMin; Kalentev et al.'s
+ * refinement with one array and no atomics), kept as comparators: whole-
+ * lattice scan/analysis passes until no label changes, the host reading a
+ * device flag after each pass.  Every labeling ends at the same canonical
+ * labels, so the chain is identical.  The comparators are update only
+ * (measurement must be off; SW_ERR_STATE otherwise), need a lattice outside
+ * any batch, run without CUDA graphs, and allocate L*L int32 more for
+ * Hawick's reference array. */
+enum sw_labeling { SW_LABEL_TILED = 0, SW_LABEL_HAWICK = 1, SW_LABEL_KALENTEV = 2 };
+int sw_set_labeling(sw_handle *h, int method);
+/* Scan passes of the last comparator sweep (0 for the tiled labeling). */
+int sw_label_passes(sw_handle *h);
+
 /* Use a different stream for subsequent work (a cudaStream_t). */
 int sw_set_stream(sw_handle *h, void *stream);
 

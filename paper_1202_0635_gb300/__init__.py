@@ -18,6 +18,7 @@ from .build import LIB as _LIB_PATH
 SW_POTTS, SW_CLOCK, SW_ISING = 0, 1, 2
 SW_OK, SW_ERR_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_NOT_CONVERGED, SW_ERR_STATE = 0, -1, -2, -3, -4, -5
 SW_INIT_UP, SW_INIT_RANDOM = 0, 1
+SW_LABEL_TILED, SW_LABEL_HAWICK, SW_LABEL_KALENTEV = 0, 1, 2
 SW_MAX_Q = 127
 SW_MAX_CLOCK_Q = 64
 SW_MAX_COUNTERS = SW_MAX_Q + SW_MAX_Q // 2 + 1 + 2
@@ -80,6 +81,8 @@ EXPORTS = [
     ("sw_get_thresholds", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
     ("sw_get_sweep", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint64)]),
     ("sw_set_sweep", ctypes.c_int, [_H, ctypes.c_uint64]),
+    ("sw_set_labeling", ctypes.c_int, [_H, ctypes.c_int]),
+    ("sw_label_passes", ctypes.c_int, [_H]),
     ("sw_set_stream", ctypes.c_int, [_H, ctypes.c_void_p]),
     ("sw_set_graph", ctypes.c_int, [_H, ctypes.c_int]),
     ("sw_profile_sweeps", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
@@ -323,6 +326,14 @@ def sw_batch_profile_sweeps(b, n):
     out = np.zeros(8, dtype=np.float32)
     m = _check(lib().sw_batch_profile_sweeps(b, int(n), _p(out, ctypes.c_float), 8))
     return [float(v) for v in out[:m]]
+
+
+def sw_set_labeling(h, method):
+    return _check(lib().sw_set_labeling(h, int(method)))
+
+
+def sw_label_passes(h):
+    return _check(lib().sw_label_passes(h))
 
 
 def sw_sweep_noalloc(L, q, model, T, seed, sweep0, n, d_spins, d_counts=None, stream=None):

@@ -1,6 +1,6 @@
 """Build libsw_gb300.so (the C-ABI library) for sm_103a with nvcc.
 
-Two translation units are compiled in parallel and linked into
+Three translation units are compiled in parallel and linked into
 paper_1202_0635_gb300/_build/libsw_gb300.so.  The build is skipped when
 the library is newer than every source.
 """
@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsw_gb300.so")
-SOURCES = ["sw_kernels.cu", "sw_api.cu"]
+SOURCES = ["sw_kernels.cu", "sw_equivalence.cu", "sw_api.cu"]
 HEADERS = ["sw_device.cuh", "sw_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -92,6 +92,12 @@ struct sw_handle {
     long long *d_merge_off = nullptr;
     unsigned int *d_ticket = nullptr;
     sw_batch *owner = nullptr;   // batch this lattice is attached to, if any
+    // Comparator labeling (SW_LABEL_HAWICK / _KALENTEV): reference array,
+    // convergence flag (device and pinned host word), passes of the last sweep.
+    int labeling = SW_LABEL_TILED;
+    int32_t *d_R = nullptr;
+    unsigned int *d_flag = nullptr, *h_flag = nullptr;
+    int last_passes = 0;
     uint32_t thr = 0;
     std::vector<uint32_t> thr_tab;
     int ncounters = 0, nclass = 0;
@@ -436,8 +442,26 @@ int autotune_shape(LaunchShape *best, int n, Timer timer)
     return SW_OK;
 }
 
+// Upper bound on the passes of a comparator labeling (the paper reports
+// fewer than ten at T_c; chains can only shorten, so this never binds for a
+// well-formed lattice).
+constexpr int kMaxLabelPasses = 100000;
+
 int enqueue_one(sw_handle *h)
 {
+    if (h->labeling != SW_LABEL_TILED) {
+        int passes = 0;
+        cudaError_t e = swgb::equivalence_sweep(h->self_batch(), h->lattice(), h->labeling, h->sm_count, h->stream,
+                                                h->d_R, h->d_flag, h->h_flag, kMaxLabelPasses, &passes);
+        if (e != cudaSuccess) return cuda_fail(e, "equivalence_sweep");
+        if (passes < 0) {
+            h->sticky = SW_ERR_NOT_CONVERGED;
+            h->sticky_msg = "comparator labeling did not converge";
+            return fail(h->sticky, "%s", h->sticky_msg.c_str());
+        }
+        h->last_passes = passes;
+        return SW_OK;
+    }
     return enqueue_sweep(h->self_batch(), h->measure, h->labels, h->sm_count, h->shape, h->stream, h->use_graph,
                          &h->graph, &h->graph_exec);
 }
@@ -455,6 +479,9 @@ void free_handle(sw_handle *h)
     if (h->d_open_count) cudaFree(h->d_open_count);
     if (h->d_open_state) cudaFree(h->d_open_state);
     if (h->d_cross) cudaFree(h->d_cross);
+    if (h->d_R) cudaFree(h->d_R);
+    if (h->d_flag) cudaFree(h->d_flag);
+    if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->d_bond) cudaFree(h->d_bond);
     if (h->d_st) cudaFree(h->d_st);
     if (h->d_ring) cudaFree(h->d_ring);
@@ -710,6 +737,7 @@ int sw_measure(sw_handle *h, sw_obs *out)
 int sw_set_measure(sw_handle *h, int on)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (on && h->labeling != SW_LABEL_TILED) return fail(SW_ERR_STATE, "the comparator labelings are update only");
     if (h->owner) return fail(SW_ERR_STATE, "lattice is attached to a batch; use sw_batch_set_measure");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
@@ -848,6 +876,7 @@ int sw_set_stream(sw_handle *h, void *stream)
 int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages)
 {
     if (!h || !ms) return fail(SW_ERR_ARG, "null argument");
+    if (h->labeling != SW_LABEL_TILED) return fail(SW_ERR_STATE, "stage profile needs the tiled labeling");
     if (n < 1 || max_stages < 1) return fail(SW_ERR_ARG, "n and max_stages must be positive");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
@@ -871,6 +900,7 @@ int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages)
 int sw_autotune(sw_handle *h, int n, int *shape_out)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (h->labeling != SW_LABEL_TILED) return fail(SW_ERR_STATE, "autotuning needs the tiled labeling");
     if (n < 1) return fail(SW_ERR_ARG, "n must be positive");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
@@ -924,6 +954,31 @@ int sw_set_launch_shape(sw_handle *h, const int *shape)
     h->shape.flip = shape[3];
     drop_graph(h);
     return SW_OK;
+}
+
+int sw_set_labeling(sw_handle *h, int method)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (method != SW_LABEL_TILED && method != SW_LABEL_HAWICK && method != SW_LABEL_KALENTEV)
+        return fail(SW_ERR_ARG, "unknown labeling %d", method);
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    if (method != SW_LABEL_TILED) {
+        if (h->owner) return fail(SW_ERR_STATE, "lattice is attached to a batch");
+        if (h->measure) return fail(SW_ERR_STATE, "the comparator labelings are update only: turn measurement off");
+        if (!h->d_flag) SW_CUDA(cudaMalloc(&h->d_flag, sizeof(unsigned int)));
+        if (!h->h_flag) SW_CUDA(cudaHostAlloc(&h->h_flag, sizeof(unsigned int), cudaHostAllocDefault));
+        if (method == SW_LABEL_HAWICK && !h->d_R) SW_CUDA(cudaMalloc(&h->d_R, (size_t)h->L * h->L * sizeof(int32_t)));
+    }
+    h->labeling = method;
+    h->last_passes = 0;
+    return SW_OK;
+}
+
+int sw_label_passes(sw_handle *h)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    return h->last_passes;
 }
 
 int sw_set_graph(sw_handle *h, int on)
@@ -1059,6 +1114,7 @@ int sw_batch_attach(sw_batch *b, sw_handle *h)
 {
     if (!b || !h) return fail(SW_ERR_ARG, "null argument");
     if (h->owner) return fail(SW_ERR_STATE, "lattice is already attached to a batch");
+    if (h->labeling != SW_LABEL_TILED) return fail(SW_ERR_STATE, "a comparator labeling cannot join a batch");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
     if (h->measure != b->measure) {

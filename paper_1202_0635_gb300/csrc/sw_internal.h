@@ -55,5 +55,19 @@ struct LaunchShape {
 constexpr int kMaxStages = 5;
 cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape,
                          cudaStream_t s, cudaEvent_t *ev = nullptr);
+// The bond kernel alone (the first stage of a sweep).
+cudaError_t launch_bonds(const Batch &b, bool measure, int sm_count, cudaStream_t s);
+
+// Comparator labelings of the paper's GPU design (Sec. 3), whole-lattice
+// iterations until no label changes.
+enum : int { kLabelTiled = 0, kLabelHawick = 1, kLabelKalentev = 2 };
+// One update-only sweep of lattice `lat` (b: its batch-of-one view) with an
+// iterated label-equivalence labeling: bonds, scan/analysis(/relabel)
+// passes until the device flag stays clear (the host reads it after every
+// pass), new spins from every cluster root's draw, sweep index advanced.
+// R: int32[L*L] reference array (Hawick only).  *passes = scan passes, or
+// -1 if max_passes ran out (then no spin is updated).
+cudaError_t equivalence_sweep(const Batch &b, const Lattice &lat, int method, int sm_count, cudaStream_t s,
+                              int32_t *R, unsigned int *d_flag, unsigned int *h_flag, int max_passes, int *passes);
 
 }  // namespace swgb

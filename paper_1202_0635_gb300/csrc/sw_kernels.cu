@@ -1247,6 +1247,16 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
     return cudaGetLastError();
 }
 
+cudaError_t launch_bonds(const Batch &b, bool measure, int sm_count, cudaStream_t s)
+{
+    const int blocks = std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM));
+    if (measure)
+        k_bonds<true><<<blocks, kBlockThreads, 0, s>>>(b);
+    else
+        k_bonds<false><<<blocks, kBlockThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape,
                          cudaStream_t s, cudaEvent_t *ev)
 {
