@@ -848,42 +848,60 @@ __device__ __forceinline__ int open_root_of(const Lattice &lat, int site, bool &
 __global__ void k_merge(Batch b)
 {
     long long lo = 0, hi = 0;
+    int rep = -1;
     Lattice lat;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < b.nmerge;
-         k += (long long)gridDim.x * blockDim.x) {
-        if (k < lo || k >= hi) {
-            const int rep = find_rep(b.merge_off, b.nrep, k);
-            lo = __ldg(b.merge_off + rep);
-            hi = __ldg(b.merge_off + rep + 1);
-            lat = b.lat[rep];
+    const unsigned lane = threadIdx.x & 31;
+    // Warp-uniform trip count: the lanes of a warp take consecutive items,
+    // so neighbouring bonds of one tile edge meet in one warp.
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < b.nmerge;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long k = base + lane;
+        bool ok = k < b.nmerge;
+        int a = 0, c2 = 0;
+        if (ok) {
+            if (k < lo || k >= hi) {
+                rep = find_rep(b.merge_off, b.nrep, k);
+                lo = __ldg(b.merge_off + rep);
+                hi = __ldg(b.merge_off + rep + 1);
+                lat = b.lat[rep];
+            }
+            const int L = lat.L, ncol = lat.tiles_x;
+            const long long kk = k - lo;
+            const long long nright = (long long)L * ncol;
+            int i, j;
+            if (kk < nright) {   // right edge of tile column c, row y (rows run fastest)
+                const int c = (int)(kk / L), y = (int)(kk % L);
+                const int tile = (y / TH) * ncol + c;
+                ok = (__ldg(lat.cross + (size_t)tile * kCrossWords + ((y % TH) >> 5)) >> (y & 31)) & 1u;
+                const int x = min((c + 1) * TW, L) - 1;
+                i = y * L + x;
+                j = y * L + (x + 1 == L ? 0 : x + 1);
+            } else {             // bottom edge of tile row rr, column x
+                const long long k2 = kk - nright;
+                const int rr = (int)(k2 / L), x = (int)(k2 % L);
+                const int tile = rr * ncol + x / TW;
+                ok = (__ldg(lat.cross + (size_t)tile * kCrossWords + 2 + ((x % TW) >> 5)) >> (x & 31)) & 1u;
+                const int y = min((rr + 1) * TH, L) - 1;
+                i = y * L + x;
+                j = (y + 1 == L ? 0 : y + 1) * L + x;
+            }
+            if (ok) {
+                bool open = true;
+                a = open_root_of(lat, i, open);
+                c2 = open_root_of(lat, j, open);
+                if (!open) {   // a crossing bond always ends at open sites
+                    record_error(lat.st, kErrInternal, i);
+                    ok = false;
+                }
+            }
         }
-        const int L = lat.L, ncol = lat.tiles_x;
-        const long long kk = k - lo;
-        const long long nright = (long long)L * ncol;
-        int i, j;
-        if (kk < nright) {
-            const int y = (int)(kk / ncol), c = (int)(kk % ncol);
-            const int tile = (y / TH) * ncol + c;
-            if (!((__ldg(lat.cross + (size_t)tile * kCrossWords + ((y % TH) >> 5)) >> (y & 31)) & 1u)) continue;
-            const int x = min((c + 1) * TW, L) - 1;
-            i = y * L + x;
-            j = y * L + (x + 1 == L ? 0 : x + 1);
-        } else {
-            const long long k2 = kk - nright;
-            const int rr = (int)(k2 / L), x = (int)(k2 % L);
-            const int tile = rr * ncol + x / TW;
-            if (!((__ldg(lat.cross + (size_t)tile * kCrossWords + 2 + ((x % TW) >> 5)) >> (x & 31)) & 1u)) continue;
-            const int y = min((rr + 1) * TH, L) - 1;
-            i = y * L + x;
-            j = (y + 1 == L ? 0 : y + 1) * L + x;
+        // Bonds of one warp that join the same two open roots need one union.
+        const unsigned vm = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const unsigned long long key = ((unsigned long long)(unsigned)a << 32) | (unsigned)c2;
+            const unsigned peers = __match_any_sync(vm, key) & __match_any_sync(vm, rep);
+            if ((unsigned)__ffs(peers) - 1u == lane) union_roots(lat.label, a, c2, lat.L * lat.L + 1, lat.st);
         }
-        bool ok = true;
-        const int a = open_root_of(lat, i, ok), c2 = open_root_of(lat, j, ok);
-        if (!ok) {   // a crossing bond always ends at open sites
-            record_error(lat.st, kErrInternal, i);
-            continue;
-        }
-        union_roots(lat.label, a, c2, L * L + 1, lat.st);
     }
 }
 
