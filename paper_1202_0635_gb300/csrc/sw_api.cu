@@ -159,6 +159,7 @@ struct sw_handle {
         b.nrep = 1;
         b.ntasks = ntasks();
         b.nmerge = nmerge();
+        b.any_clock = model == SW_CLOCK;
         return b;
     }
 };
@@ -180,6 +181,7 @@ struct sw_batch {
     unsigned int *d_ticket = nullptr;
     int ntasks = 0;
     long long nmerge = 0;
+    bool any_clock = false;
     bool dirty = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -194,6 +196,7 @@ struct sw_batch {
         b.nrep = (int)reps.size();
         b.ntasks = ntasks;
         b.nmerge = nmerge;
+        b.any_clock = any_clock;
         return b;
     }
 };
@@ -1032,9 +1035,12 @@ static int rebuild_batch(sw_batch *b)
         task_off[i + 1] = task_off[i] + b->reps[i]->ntasks();
         merge_off[i + 1] = merge_off[i] + b->reps[i]->nmerge();
     }
-    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge) drop_batch_graph(b);
+    bool any_clock = false;
+    for (int i = 0; i < n; ++i) any_clock = any_clock || b->reps[i]->model == SW_CLOCK;
+    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge || any_clock != b->any_clock) drop_batch_graph(b);
     b->ntasks = task_off[n];
     b->nmerge = merge_off[n];
+    b->any_clock = any_clock;
     if (n) {
         SW_CUDA(cudaMemcpyAsync(b->d_lat, lat.data(), sizeof(Lattice) * n, cudaMemcpyHostToDevice, b->stream));
         SW_CUDA(cudaMemcpyAsync(b->d_task_off, task_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
@@ -1456,6 +1462,7 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     b.nrep = 1;
     b.ntasks = task_off[1];
     b.nmerge = merge_off[1];
+    b.any_clock = model == SW_CLOCK;
 
     // The array keeps whatever the previous call left: reset everything that
     // must start from a known value (sweep index, error word, ticket,

@@ -66,6 +66,7 @@ struct Batch {
     int nrep;
     int ntasks;
     long long nmerge;
+    int any_clock;                 // a clock lattice is present (selects the kernel variant that measures it)
 };
 
 // Philox-4x32-10 (Salmon et al., SC'11).  Each round takes two 32x32->64

@@ -250,7 +250,7 @@ __device__ __forceinline__ void count_pair_classes(unsigned int *hist, const uin
 // bonds and the bond classes of the incoming configuration (the previous
 // sweep's result).
 // ---------------------------------------------------------------------------
-template <bool MEASURE>
+template <bool MEASURE, bool CLOCK_MEASURE>
 __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
 {
     // Clock model: threshold of two projection magnitudes r_a, r_b on the
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                 if (!lat.clock) {
                     block_add<kBlockThreads>(prev + lat.q + 1, unequal, red);
                     block_add<kBlockThreads>(prev + lat.q + 0, pairs - unequal, red);
-                } else {
+                } else if (CLOCK_MEASURE) {
                     __syncthreads();
                     const int nc = lat.nclass;
                     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
@@ -408,6 +408,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                         unequal += __popc(~eqR & V) + __popc(~eqD & V);
                         pairs += 2u * (unsigned)ncols;
                     }
+                } else if (!CLOCK_MEASURE) {
+                    record_error(lat.st, kErrInternal, 0);   // a clock lattice needs the clock variant
                 } else if (lat.nclass <= 8) {
                     // Up to 8 classes: 16-bit counters packed in two words per
                     // thread, reduced over the warp once per tile.
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                         add_hist_any(hist_class, clock_bond_class(s0, byte_at(dn, c), q), v);
                     }
                 }
-                if (clock) {
+                if (CLOCK_MEASURE && clock) {
                     // Correlation pairs (i, i + r x), (i, i + r y) at r = L/4 and
                     // r = L/2 (Sec. 4, G(r,T)) of the incoming configuration.
 #pragma unroll 1
@@ -1219,7 +1221,11 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
         if (ev) cudaEventRecord(ev[nev++], s);
     };
     mark();
-    k_bonds<MEASURE><<<std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM)), kBlockThreads, 0, s>>>(b);
+    const int bblocks = std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM));
+    if (MEASURE && b.any_clock)
+        k_bonds<MEASURE, true><<<bblocks, kBlockThreads, 0, s>>>(b);
+    else
+        k_bonds<MEASURE, false><<<bblocks, kBlockThreads, 0, s>>>(b);
     mark();
     k_label_tiles<MEASURE, LABELS><<<std::max(1, std::min(b.ntasks, sm_count * shape.label)), kBlockThreads, 0, s>>>(b);
     mark();
@@ -1268,10 +1274,12 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
 cudaError_t launch_bonds(const Batch &b, bool measure, int sm_count, cudaStream_t s)
 {
     const int blocks = std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM));
-    if (measure)
-        k_bonds<true><<<blocks, kBlockThreads, 0, s>>>(b);
+    if (!measure)
+        k_bonds<false, false><<<blocks, kBlockThreads, 0, s>>>(b);
+    else if (b.any_clock)
+        k_bonds<true, true><<<blocks, kBlockThreads, 0, s>>>(b);
     else
-        k_bonds<false><<<blocks, kBlockThreads, 0, s>>>(b);
+        k_bonds<true, false><<<blocks, kBlockThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
