@@ -39,10 +39,10 @@ L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 # Algorithmic bytes per site of each stage (q = 2 Potts, measurement on):
 # the bond stage reads the int8 spin and writes two bond bits, the
 # labeling stage reads the bond bits and writes a 2-byte code, the flip
-# stage reads the code and writes the int8 spin.  The merge and flattening
-# stages touch only tile-border data.
-STAGES = ["bonds", "label", "merge", "flatten", "flip"]
-ALG_BYTES_PER_SITE = {"bonds": 1.25, "label": 2.25, "merge": None, "flatten": None, "flip": 3.0}
+# stage reads the code and writes the int8 spin.  The merge stage touches
+# only tile-border data.
+STAGES = ["bonds", "label", "merge", "flip"]
+ALG_BYTES_PER_SITE = {"bonds": 1.25, "label": 2.25, "merge": None, "flip": 3.0}
 # Whole-sweep byte model of the method (int8 spins, int32 labels
 # materialised): spin read + label write + label read + spin write.
 SWEEP_BYTES_PER_SITE = 10.0

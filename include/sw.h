@@ -8,8 +8,8 @@
  * embedded clusters, Sec. 4).  Every stage of a sweep runs as a CUDA kernel
  * on the calling thread's current device:
  *   bond activation  -> tile-local cluster labeling in shared memory
- *   -> boundary merge (atomicMin union-find) -> flatten + per-cluster draw
- *   + spin write -> integer reductions of the observables.
+ *   -> boundary merge (atomicMin union-find) -> cluster roots, per-cluster
+ *   draw and spin write -> integer reductions of the observables.
  *
  * Conventions (identical, by specification, to the CPU oracle's):
  *   site i = y*L + x (row-major); site i owns the bond to (y, x+1 mod L)
@@ -180,7 +180,7 @@ int sw_get_sweep(sw_handle *h, uint64_t *out);
 int sw_set_sweep(sw_handle *h, uint64_t t);
 
 /* Launch shape: resident blocks per SM requested for the four kernels of
- * a sweep, shape[4] = {labeling, merge, flatten, flip}, each in [1, 64].
+ * a sweep, shape[4] = {labeling, merge, flip, bonds}, each in [1, 64].
  * Results never depend on it.  sw_autotune times every candidate (n real
  * sweeps each, they advance the chain like any others), keeps the fastest
  * per kernel, caches it per (device, work size) for the process, and writes
@@ -214,9 +214,9 @@ int sw_set_graph(sw_handle *h, int on);
 /* Tracing: run n sweeps with CUDA events recorded on the handle's stream
  * around every kernel (direct launches) and write the mean device time per
  * sweep of each stage in milliseconds to ms[0 .. stages-1]:
- *   0 bond activation + tile-local labeling (+ bond classes of the incoming
- *     configuration), 1 merge across tile edges, 2 root flattening,
- *   3 cluster draws + spin write (+ state counts).
+ *   0 bond activation (+ bond classes of the incoming configuration),
+ *   1 tile-local labeling and closed-cluster draws, 2 merge across tile
+ *   edges, 3 open-cluster roots and draws + spin write (+ state counts).
  * The sweeps count like any others.  Returns the number of stages (>0). */
 int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages);
 

@@ -422,8 +422,8 @@ int autotune_shape(LaunchShape *best, int n, Timer timer)
     static const int cand_label[] = {4, 6, 8};
     static const int cand_other[] = {4, 8, 16, 32};
     double ms[swgb::kMaxStages];
-    // Timed stages 1..4 are the labeling, merge, flatten and flip kernels
-    // (stage 0, the bond kernel, has a fixed shape).
+    // Timed stages: 0 bonds, 1 labeling, 2 merge, 3 flip.
+    static const int stage_of[4] = {1, 2, 3, 0};   // tuned in the order label, merge, flip, bonds
     for (int k = 0; k < 4; ++k) {
         const int *cand = k == 0 ? cand_label : cand_other;
         const int ncand = k == 0 ? 3 : 4;
@@ -431,12 +431,12 @@ int autotune_shape(LaunchShape *best, int n, Timer timer)
         LaunchShape pick = *best;
         for (int i = 0; i < ncand; ++i) {
             LaunchShape trial = *best;
-            int *field = k == 0 ? &trial.label : k == 1 ? &trial.merge : k == 2 ? &trial.flatten : &trial.flip;
+            int *field = k == 0 ? &trial.label : k == 1 ? &trial.merge : k == 2 ? &trial.flip : &trial.bonds;
             *field = cand[i];
             int rc = timer(trial, n, ms);
             if (rc != SW_OK) return rc;
-            if (ms[k + 1] < best_ms) {
-                best_ms = ms[k + 1];
+            if (ms[stage_of[k]] < best_ms) {
+                best_ms = ms[stage_of[k]];
                 pick = trial;
             }
         }
@@ -940,8 +940,8 @@ int sw_autotune(sw_handle *h, int n, int *shape_out)
     if (shape_out) {
         shape_out[0] = best.label;
         shape_out[1] = best.merge;
-        shape_out[2] = best.flatten;
-        shape_out[3] = best.flip;
+        shape_out[2] = best.flip;
+        shape_out[3] = best.bonds;
     }
     return drain(h);
 }
@@ -953,8 +953,8 @@ int sw_set_launch_shape(sw_handle *h, const int *shape)
         if (shape[k] < 1 || shape[k] > 64) return fail(SW_ERR_ARG, "blocks per SM must be in [1, 64]");
     h->shape.label = shape[0];
     h->shape.merge = shape[1];
-    h->shape.flatten = shape[2];
-    h->shape.flip = shape[3];
+    h->shape.flip = shape[2];
+    h->shape.bonds = shape[3];
     drop_graph(h);
     return SW_OK;
 }
@@ -1282,8 +1282,8 @@ int sw_batch_autotune(sw_batch *b, int n, int *shape_out)
     if (shape_out) {
         shape_out[0] = best.label;
         shape_out[1] = best.merge;
-        shape_out[2] = best.flatten;
-        shape_out[3] = best.flip;
+        shape_out[2] = best.flip;
+        shape_out[3] = best.bonds;
     }
     return sw_batch_synchronize(b);
 }
@@ -1295,8 +1295,8 @@ int sw_batch_set_launch_shape(sw_batch *b, const int *shape)
         if (shape[k] < 1 || shape[k] > 64) return fail(SW_ERR_ARG, "blocks per SM must be in [1, 64]");
     b->shape.label = shape[0];
     b->shape.merge = shape[1];
-    b->shape.flatten = shape[2];
-    b->shape.flip = shape[3];
+    b->shape.flip = shape[2];
+    b->shape.bonds = shape[3];
     drop_batch_graph(b);
     return SW_OK;
 }

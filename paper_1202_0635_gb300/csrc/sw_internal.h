@@ -31,7 +31,7 @@ constexpr uint16_t kCodeClosed = 0x8000;
 
 // Bond-mask words per tile (right and down bonds of 64 rows, 2 words a row).
 constexpr int kBondWords = 2 * kTileH * (kTileW / 32);
-// Resident blocks per SM requested for the bond kernel (not autotuned).
+// Resident blocks per SM requested for the bond kernel outside a sweep.
 constexpr int kBondBlocksPerSM = 16;
 
 // Counter rows kept on the device; the host drains them before the ring
@@ -45,14 +45,14 @@ cudaError_t launch_pending_classes(const Lattice &lat, int sm_count, cudaStream_
 // Number of spins outside [0, q) is added to *bad (device word).
 cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_count, cudaStream_t s);
 // Launch shape of a sweep: resident blocks per SM requested for the
-// labeling, merge, flatten and flip kernels (the grids never exceed the
-// work).  Any shape gives the same results; only the speed differs.
+// labeling, merge, flip and bond kernels (the grids never exceed the work).
+// Any shape gives the same results; only the speed differs.
 struct LaunchShape {
-    int label = 8, merge = 16, flatten = 16, flip = 16;
+    int label = 8, merge = 16, flip = 16, bonds = kBondBlocksPerSM;
 };
 // ev (optional): events recorded before the first and after every kernel of
-// the sweep (kMaxStages + 1 entries): bonds, labeling, merge, flatten, flip.
-constexpr int kMaxStages = 5;
+// the sweep (kMaxStages + 1 entries): bonds, labeling, merge, flip.
+constexpr int kMaxStages = 4;
 cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape,
                          cudaStream_t s, cudaEvent_t *ev = nullptr);
 // The bond kernel alone (the first stage of a sweep).

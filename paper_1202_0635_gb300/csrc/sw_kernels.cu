@@ -1,7 +1,7 @@
 // sw_kernels.cu -- the kernels of one Swendsen-Wang sweep on sm_103a.
 //
 // One sweep (Komura & Okabe, arXiv:1202.0635, Sec. 2 steps (i)-(viii);
-// clock model: Sec. 4 embedded clusters) is five launches over the 64 x 64
+// clock model: Sec. 4 embedded clusters) is four launches over the 64 x 64
 // tiles of every lattice of a batch (a single lattice is a batch of one).
 // A block owns one tile of one lattice at a time ("task"), so per-lattice
 // counters reduce per block.
@@ -24,12 +24,12 @@
 //   k_merge        joins the open roots across every active bond that
 //                  crosses a tile edge or the periodic wrap (atomicMin,
 //                  larger root under smaller).
-//   k_flatten      points every open root straight at its cluster root
-//                  (the smallest site index of the cluster, Sec. 2 "proper
-//                  label") and counts those roots.
-//   k_flip_tiles   draws the new state of every open cluster root, writes
-//                  all spins, counts states; its last block advances the
-//                  sweep index of every lattice of the batch.
+//   k_flip_tiles   finds the cluster root of every open component (the
+//                  smallest site index of the cluster, Sec. 2 "proper
+//                  label"), which draws the cluster's new state; writes all
+//                  spins, counts states and the clusters rooted in the tile;
+//                  its last block advances the sweep index of every lattice
+//                  of the batch.
 #include "sw_internal.h"
 
 namespace swgb {
@@ -907,52 +907,6 @@ __global__ void k_merge(Batch b)
     }
 }
 
-// ---------------------------------------------------------------------------
-// k_flatten: every open root -> its cluster root, which draws the cluster's
-// new state (Potts) or reflection flag (clock) into the tile's open-state
-// table; the open list then holds the cluster roots.  Counts cluster roots.
-// One warp per tile.
-// ---------------------------------------------------------------------------
-template <bool MEASURE>
-__global__ void __launch_bounds__(kBlockThreads) k_flatten(Batch b)
-{
-    __shared__ unsigned int red[32];
-    __shared__ __align__(16) Lattice lat;
-    __shared__ unsigned long long s_t;
-    unsigned int roots = 0;
-    int cur = -1;
-    auto flush = [&]() {
-        if (MEASURE && cur >= 0) block_add<kBlockThreads>(ring_row(lat, s_t) + lat.q + lat.nclass + 1, roots, red);
-        roots = 0;
-        __syncthreads();
-    };
-    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
-        const int rep = find_rep(b.task_off, b.nrep, task);
-        if (rep != cur) {
-            flush();
-            load_lattice(&lat, b.lat + rep);
-            __syncthreads();
-            if (threadIdx.x == 0) s_t = read_u64(&lat.st->sweep);
-            __syncthreads();
-            cur = rep;
-        }
-        const int tile = task - __ldg(b.task_off + rep);
-        const int cap = lat.L * lat.L + 1;
-        const int n = lat.open_count[tile];
-        for (int s = threadIdx.x; s < n; s += blockDim.x) {
-            const size_t k = (size_t)tile * kOpenSlots + s;
-            const int r = lat.open_list[k];
-            const int root = find_root_halving(lat.label, r, cap, lat.st);
-            if (root != r) lat.label[r] = root;
-            else ++roots;
-            const uint32_t u = draw4(lat, (uint32_t)root, s_t, kTagState).x;
-            lat.open_state[k] = lat.clock ? (uint8_t)(u >> 31) : (uint8_t)mulhi_q(u, lat.q);
-            lat.open_list[k] = root;
-        }
-    }
-    flush();
-}
-
 // Last block of the sweep's final kernel: for every lattice of the batch,
 // record that the incoming configuration's classes were counted, zero the
 // next counter row and advance the sweep index (every block has read it).
@@ -983,8 +937,9 @@ __device__ void finish_sweep(const Batch &b)
 }
 
 // ---------------------------------------------------------------------------
-// k_flip_tiles: new states of open clusters, all spin writes, state counts.
-// One block per tile, one warp per quadrant.
+// k_flip_tiles: the cluster roots and new states of the tile's open
+// components, all spin writes, state counts.  One block per tile, one warp
+// per quadrant.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS>
 __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
@@ -992,6 +947,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
     __shared__ __align__(16) unsigned char tab[kOpenSlots];
     __shared__ int rootg[LABELS ? kOpenSlots : 1];
     __shared__ unsigned int hist_state[SW_MAX_Q + 1];
+    __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
@@ -1000,9 +956,11 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
     // q <= 8: state counts of this lane, 16 bits per state (states 0-3, 4-7);
     // q == 2: sites in cnt_hi, sites in state 1 in cnt_lo.
     unsigned long long cnt_lo = 0, cnt_hi = 0;
+    unsigned int open_roots = 0;   // clusters reaching a tile border, counted at their root
     int cur = -1;
     auto flush = [&]() {
         if (MEASURE && cur >= 0) {
+            block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass + 1, open_roots, red);
             if (lat.q == 2) {
                 const unsigned int n1 = __reduce_add_sync(FULL, (unsigned int)cnt_lo);
                 const unsigned int n = __reduce_add_sync(FULL, (unsigned int)cnt_hi);
@@ -1024,6 +982,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
                 if (hist_state[k]) atomicAdd(row + k, (unsigned long long)hist_state[k]);
         }
         cnt_lo = cnt_hi = 0;
+        open_roots = 0;
         __syncthreads();
     };
     for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
@@ -1059,13 +1018,22 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
             cw[k] = v ? *reinterpret_cast<const uint2 *>(lat.code + site0) : make_uint2(0u, 0u);
             sw[k] = (clock && v) ? *reinterpret_cast<const uint32_t *>(lat.spin + site0) : 0u;
         }
-        // The tile's open-state table (kOpenSlots bytes) into shared memory.
+        // Every open component of the tile belongs to a cluster whose root
+        // (its smallest site, after the merge) draws the new state (Potts) or
+        // the reflection flag (clock), Sec. 2 (v)-(vii) / Sec. 4, into the
+        // tile's table.  A cluster is counted once, by the tile holding its root.
         {
             const size_t k0 = (size_t)tile * kOpenSlots;
-            for (int i = threadIdx.x; i < kOpenSlots / 4; i += blockDim.x)
-                reinterpret_cast<uint32_t *>(tab)[i] = __ldg(reinterpret_cast<const uint32_t *>(lat.open_state + k0) + i);
-            if (LABELS)
-                for (int s = threadIdx.x; s < kOpenSlots; s += blockDim.x) rootg[LABELS ? s : 0] = lat.open_list[k0 + s];
+            const int n = lat.open_count[tile];
+            const int cap = L * L + 1;
+            for (int s = threadIdx.x; s < n; s += blockDim.x) {
+                const int r = lat.open_list[k0 + s];
+                const int root = find_root_halving(lat.label, r, cap, lat.st);
+                if (MEASURE && root == r) ++open_roots;
+                const uint32_t u = draw4(lat, (uint32_t)root, ctx.t, kTagState).x;
+                tab[s] = clock ? (unsigned char)(u >> 31) : (unsigned char)mulhi_q(u, q);
+                if (LABELS) rootg[LABELS ? s : 0] = root;
+            }
         }
         __syncthreads();
 
@@ -1221,7 +1189,7 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
         if (ev) cudaEventRecord(ev[nev++], s);
     };
     mark();
-    const int bblocks = std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM));
+    const int bblocks = std::max(1, std::min(b.ntasks, sm_count * shape.bonds));
     if (MEASURE && b.any_clock)
         k_bonds<MEASURE, true><<<bblocks, kBlockThreads, 0, s>>>(b);
     else
@@ -1232,8 +1200,6 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
     const int mblocks =
         (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * shape.merge));
     k_merge<<<mblocks, 256, 0, s>>>(b);
-    mark();
-    k_flatten<MEASURE><<<std::max(1, std::min(b.ntasks, sm_count * shape.flatten)), kBlockThreads, 0, s>>>(b);
     mark();
     k_flip_tiles<MEASURE, LABELS><<<std::max(1, std::min(b.ntasks, sm_count * shape.flip)), kBlockThreads, 0, s>>>(b);
     mark();

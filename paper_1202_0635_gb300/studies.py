@@ -1,7 +1,7 @@
 """Temperature scans on the GPU engine (Komura & Okabe, arXiv:1202.0635,
 Sec. 4): the moment ratio U(T) = <M^4>/<M^2>^2 of several sizes (Eq. U; the
-crossing of the curves marks the critical point, Fig. 3), the time per spin
-flip against T with its per-stage split (Figs. 2 and 5), and the
+crossing of the curves marks the critical point, Fig. 4), the time per spin
+flip against T with its per-stage split (Figs. 3 and 5), and the
 correlation ratio R(T) = G(L/2)/G(L/4) of the clock model (Fig. 6).
 
 Every (L, T) point is its own lattice; all of them advance together in one
@@ -77,7 +77,7 @@ def timing(q, model, L, temps, sweeps=20, equil=50, seed=1):
     """Per-stage device time per spin flip (ns) of one lattice at each T,
     CUDA events around every kernel of direct-launched sweeps."""
     sw = _sw()
-    stages = ["bonds", "label", "merge", "flatten", "flip"]
+    stages = ["bonds", "label", "merge", "flip"]
     out = []
     for T in temps:
         lat = sw.Lattice(L, q, model, T, seed, init=sw.SW_INIT_RANDOM)
