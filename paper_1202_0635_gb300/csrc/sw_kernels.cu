@@ -207,28 +207,75 @@ __device__ __forceinline__ void load_partners(const int8_t *spin, int L, int y, 
     }
 }
 
+// Clock classes min(dk, q - dk) of four state pairs at once (the bytes of
+// a and b; q <= 15, so every class is below 8); a state outside [0, q)
+// counts as state 0.
+__device__ __forceinline__ uint32_t clock_classes4(uint32_t a, uint32_t b, uint32_t q4)
+{
+    a &= __vcmpltu4(a, q4);
+    b &= __vcmpltu4(b, q4);
+    uint32_t d = __vsub4(__vadd4(a, q4), b);   // a - b + q, in [1, 2q - 1]
+    d = __vsub4(d, __vcmpgeu4(d, q4) & q4);     // (a - b) mod q
+    return __vminu4(d, __vsub4(q4, d));
+}
+
+// Tally of pair classes below 8, four pairs (bytes) at a time: how many
+// pairs have each combination of class bits set (bit planes), from which
+// the count of every class follows by inclusion-exclusion.
+struct ClassTally {
+    unsigned n = 0;                              // pairs
+    unsigned m[7] = {0, 0, 0, 0, 0, 0, 0};      // m[S - 1]: pairs whose class has all bits of S (S = 1..7)
+    __device__ __forceinline__ void add4(uint32_t cls)
+    {
+        const uint32_t b0 = cls & 0x01010101u, b1 = (cls >> 1) & 0x01010101u, b2 = (cls >> 2) & 0x01010101u;
+        n += 4u;
+        m[0] += __popc(b0);
+        m[1] += __popc(b1);
+        m[2] += __popc(b0 & b1);
+        m[3] += __popc(b2);
+        m[4] += __popc(b0 & b2);
+        m[5] += __popc(b1 & b2);
+        m[6] += __popc(b0 & b1 & b2);
+    }
+    // Pairs of class d: sum over S containing d of (-1)^|S - d| N_S.
+    __device__ __forceinline__ unsigned count(int d) const
+    {
+        int c = 0;
+#pragma unroll
+        for (int S = 0; S < 8; ++S) {
+            if ((S & d) != d) continue;
+            const int ns = S ? (int)m[S - 1] : (int)n;
+            c += (__popc(S ^ d) & 1) ? -ns : ns;
+        }
+        return (unsigned)c;
+    }
+    // Warp sum of every class count into a shared histogram (all 32 lanes).
+    __device__ __forceinline__ void flush(unsigned int *hist, int nclass) const
+    {
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const unsigned int v = __reduce_add_sync(FULL, count(d));
+            if ((threadIdx.x & 31) == 0 && v && d < nclass) atomicAdd(&hist[d], v);
+        }
+    }
+};
+
 // Clock classes min(dk, q - dk) of the pairs (row byte c, px byte c) and
 // (row byte c, py byte c), c < ncols, into a shared histogram.  Must be
 // called by all 32 lanes of the warp.
 __device__ __forceinline__ void count_pair_classes(unsigned int *hist, const uint32_t (&wd)[8], const uint32_t (&px)[8],
                                                    const uint32_t (&py)[8], int ncols, bool rv, int q, int nclass)
 {
-    if (nclass <= 8) {
-        unsigned long long c_lo = 0, c_hi = 0;   // 16-bit counters, classes 0-3 and 4-7
+    if (nclass <= 8) {   // q <= 15: four pairs per word
+        const uint32_t q4 = (uint32_t)q * 0x01010101u;
+        ClassTally t;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            if (!(rv && c < ncols)) continue;
-            const int s0 = byte_at(wd, c);
-            const int d0 = clock_bond_class(s0, byte_at(px, c), q), d1 = clock_bond_class(s0, byte_at(py, c), q);
-            (d0 < 4 ? c_lo : c_hi) += 1ull << (16 * (d0 & 3));
-            (d1 < 4 ? c_lo : c_hi) += 1ull << (16 * (d1 & 3));
+        for (int k = 0; k < 8; ++k) {
+            if (!(rv && 4 * k < ncols)) continue;   // ncols % 4 == 0
+            t.add4(clock_classes4(wd[k], px[k], q4));
+            t.add4(clock_classes4(wd[k], py[k], q4));
         }
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const unsigned long long w = d < 4 ? c_lo : c_hi;
-            const unsigned int v = __reduce_add_sync(FULL, (unsigned int)((w >> (16 * (d & 3))) & 0xFFFFull));
-            if ((threadIdx.x & 31) == 0 && v) atomicAdd(&hist[d], v);
-        }
+        t.flush(hist, nclass);
     } else {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
@@ -411,24 +458,18 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                 } else if (!CLOCK_MEASURE) {
                     record_error(lat.st, kErrInternal, 0);   // a clock lattice needs the clock variant
                 } else if (lat.nclass <= 8) {
-                    // Up to 8 classes: 16-bit counters packed in two words per
-                    // thread, reduced over the warp once per tile.
-                    unsigned long long c_lo = 0, c_hi = 0;
+                    // q <= 15: the classes of four pairs per word, tallied by
+                    // bit planes and reduced over the warp once per tile.
+                    const uint32_t q4 = (uint32_t)q * 0x01010101u;
+                    ClassTally tl;
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        if (!(rv && c < ncols)) continue;
-                        const int s0 = byte_at(wd, c);
-                        const int s1 = (c + 1 < ncols) ? byte_at(wd, (c + 1) & 31) : (int)sr;
-                        const int d0 = clock_bond_class(s0, s1, q), d1 = clock_bond_class(s0, byte_at(dn, c), q);
-                        (d0 < 4 ? c_lo : c_hi) += 1ull << (16 * (d0 & 3));
-                        (d1 < 4 ? c_lo : c_hi) += 1ull << (16 * (d1 & 3));
+                    for (int k = 0; k < 8; ++k) {
+                        if (!(rv && 4 * k < ncols)) continue;   // ncols % 4 == 0
+                        const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
+                        tl.add4(clock_classes4(wd[k], __funnelshift_r(wd[k], nxt, 8), q4));
+                        tl.add4(clock_classes4(wd[k], dn[k], q4));
                     }
-#pragma unroll
-                    for (int d = 0; d < 8; ++d) {
-                        const unsigned long long w = d < 4 ? c_lo : c_hi;
-                        const unsigned int v = __reduce_add_sync(FULL, (unsigned int)((w >> (16 * (d & 3))) & 0xFFFFull));
-                        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&hist_class[d], v);
-                    }
+                    tl.flush(hist_class, lat.nclass);
                 } else {
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
