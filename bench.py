@@ -15,6 +15,7 @@ CPU oracle (test infrastructure) on the same workload, on rank 0 only.
 """
 import argparse
 import ctypes
+import datetime
 import json
 import math
 import os
@@ -63,29 +64,43 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons every 200 ms."""
-
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock and throttle-reason samples (every 100 ms) while the
+    sweeps run.  Started before the warm-up and waited for, so that it is
+    sampling when the timed region begins; summary() keeps the samples
+    taken within 0.25 s of the timed region (mark_start / mark_end)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    MARGIN_S = 0.25
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.tmp = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.tmp.name) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
 
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
     def __exit__(self, *exc):
         if self.proc is not None:
+            time.sleep(0.15)   # one more sample after the timed region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -101,17 +116,29 @@ class ClockSampler:
         with open(self.tmp.name) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 10:
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        ts = None
+                    rows.append((ts, parts[1:]))
         os.unlink(self.tmp.name)
-        if not rows:
+        if self.t0 is not None and self.t1 is not None:
+            near = [r for ts, r in rows if ts is not None and self.t0 - self.MARGIN_S <= ts <= self.t1 + self.MARGIN_S]
+        else:
+            near = []
+        window = "timed region +- %.2f s" % self.MARGIN_S
+        if not near:   # fall back to every sample of the run
+            near = [r for _, r in rows]
+            window = "whole run"
+        if not near:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in near if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in near if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in near for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(near), "window": window}
 
 
 def dist_setup():
@@ -309,24 +336,27 @@ def run_ours(args, world, rank, local):
         with torch.cuda.stream(stream):
             flush.add_(1)
 
-    for _ in range(args.warmup):
-        flush_l2()
-        lat.sweep(1)
-    sw.sw_synchronize(lat.h)
+    clk = ClockSampler(torch.cuda.current_device())
+    with clk:   # sampling from before the warm-up to after the timed region
+        for _ in range(args.warmup):
+            flush_l2()
+            lat.sweep(1)
+        sw.sw_synchronize(lat.h)
 
-    # ---- timed region: K sweeps, L2 flushed before each, CUDA events on the lattice stream
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(torch.cuda.current_device()) as clk:
+        # ---- timed region: K sweeps, L2 flushed before each, CUDA events on the lattice stream
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
         for k in range(args.steps):
             flush_l2()
             starts[k].record(stream)
             lat.sweep(1)
             ends[k].record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark_end()
         if dist is not None:
             dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -452,7 +482,7 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -80,7 +80,6 @@ struct sw_handle {
     uint32_t *d_thr_tab = nullptr;
     uint16_t *d_code = nullptr;
     int32_t *d_open_list = nullptr, *d_open_count = nullptr;
-    uint8_t *d_open_state = nullptr;
     uint32_t *d_cross = nullptr;
     uint32_t *d_bond = nullptr;
     int tiles_x = 0, tiles_y = 0;
@@ -132,7 +131,6 @@ struct sw_handle {
         lat.code = d_code;
         lat.open_list = d_open_list;
         lat.open_count = d_open_count;
-        lat.open_state = d_open_state;
         lat.cross = d_cross;
         lat.bond = d_bond;
         lat.tiles_x = tiles_x;
@@ -480,7 +478,6 @@ void free_handle(sw_handle *h)
     if (h->d_code) cudaFree(h->d_code);
     if (h->d_open_list) cudaFree(h->d_open_list);
     if (h->d_open_count) cudaFree(h->d_open_count);
-    if (h->d_open_state) cudaFree(h->d_open_state);
     if (h->d_cross) cudaFree(h->d_cross);
     if (h->d_R) cudaFree(h->d_R);
     if (h->d_flag) cudaFree(h->d_flag);
@@ -567,8 +564,6 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
         return bail(e, "cudaMalloc(open roots)");
     if ((e = cudaMalloc(&h->d_open_count, ntiles * sizeof(int32_t))) != cudaSuccess)
         return bail(e, "cudaMalloc(open counts)");
-    if ((e = cudaMalloc(&h->d_open_state, ntiles * swgb::kOpenSlots)) != cudaSuccess)
-        return bail(e, "cudaMalloc(open states)");
     if ((e = cudaMalloc(&h->d_cross, ntiles * swgb::kCrossWords * sizeof(uint32_t))) != cudaSuccess)
         return bail(e, "cudaMalloc(crossing bonds)");
     if ((e = cudaMalloc(&h->d_bond, ntiles * swgb::kBondWords * sizeof(uint32_t))) != cudaSuccess)
@@ -1316,7 +1311,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the working buffers inside the shared array, sized for
 // the largest accepted lattice (SW_NOALLOC_MAX_L).
 struct NoallocLayout {
-    size_t label, code, open_list, open_state, open_count, cross, bond, ring, thr_tab, st, lat, task_off,
+    size_t label, code, open_list, open_count, cross, bond, ring, thr_tab, st, lat, task_off,
         merge_off, ticket, total;
 };
 constexpr int kNoallocRingSlots = 128;   // counter rows; longer calls are drained in chunks
@@ -1331,7 +1326,6 @@ constexpr NoallocLayout noalloc_layout()
     o.label = at;      at = align256(at + sites * sizeof(int32_t));
     o.code = at;       at = align256(at + sites * sizeof(uint16_t));
     o.open_list = at;  at = align256(at + tiles * swgb::kOpenSlots * sizeof(int32_t));
-    o.open_state = at; at = align256(at + tiles * swgb::kOpenSlots);
     o.open_count = at; at = align256(at + tiles * sizeof(int32_t));
     o.cross = at;      at = align256(at + tiles * swgb::kCrossWords * sizeof(uint32_t));
     o.bond = at;       at = align256(at + tiles * swgb::kBondWords * sizeof(uint32_t));
@@ -1419,7 +1413,6 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     lat.label = (int32_t *)(base + kNoalloc.label);
     lat.code = (uint16_t *)(base + kNoalloc.code);
     lat.open_list = (int32_t *)(base + kNoalloc.open_list);
-    lat.open_state = base + kNoalloc.open_state;
     lat.open_count = (int32_t *)(base + kNoalloc.open_count);
     lat.cross = (uint32_t *)(base + kNoalloc.cross);
     lat.bond = (uint32_t *)(base + kNoalloc.bond);

@@ -41,8 +41,6 @@ struct Lattice {
     int32_t *label;             // L*L words: union-find parents of open tile roots; debug labels
     uint16_t *code;             // L*L per-site codes written by the labeling stage
     int32_t *open_list;         // tiles x kOpenSlots global indices of open tile roots
-                                // (after the flatten stage: their cluster roots)
-    uint8_t *open_state;        // tiles x kOpenSlots new state / reflect flag of each open root's cluster
     int32_t *open_count;        // tiles
     uint32_t *cross;            // tiles x 2 words: active crossing bonds (right edge rows, bottom edge columns)
     uint32_t *bond;             // tiles x 256 words: a tile's right-bond masks (64 rows x 2 words), then
@@ -163,23 +161,6 @@ __device__ __forceinline__ void union_roots(int32_t *label, int a, int b, int ca
         }
     }
     record_error(st, kErrUnionCap, a);
-}
-
-// Read-only root chase (no concurrent writers).
-__device__ __forceinline__ int find_root_ro(const int32_t *__restrict__ label, int x, int cap, DevState *st)
-{
-    const long long t0 = clock64();
-    for (int it = 0; it < cap; ++it) {
-        const int p = __ldg(label + x);
-        if (p == x) return x;
-        x = p;
-        if ((it & 255) == 255 && clock64() - t0 > kLoopBudgetCycles) {
-            record_error(st, kErrTimeBudget, x);
-            return x;
-        }
-    }
-    record_error(st, kErrFindCap, x);
-    return x;
 }
 
 // A state outside [0, q) (only possible through a caller writing the spin

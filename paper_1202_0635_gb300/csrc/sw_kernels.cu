@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         }
         __syncthreads();
 
-        // ===== phase B: labels, quadrant by quadrant (warp), lane = column ======
+        // ===== labels, quadrant by quadrant (warp), lane = column ===============
         // Row by row, every site carries the label of the site above it when
         // the two are bonded.  A run (maximal horizontally bonded segment of
         // the row) takes the label carried by its first such site; a run with

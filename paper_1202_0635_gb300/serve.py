@@ -29,14 +29,14 @@ from . import workloads
 
 def job_bytes(L, q, model):
     """Device bytes one resident lattice holds (spins int8, codes uint16,
-    labels int32, per-tile bond masks / open lists / states / crossing words,
+    labels int32, per-tile bond masks / open lists / crossing words,
     counter ring)."""
     n = L * L
     tiles = ((L + 63) // 64) ** 2
     nclass = q // 2 + 1 if model == 1 else 2
     ring = 1024 * (q + nclass + 2 + (2 * nclass if model == 1 else 0)) * 8
     table = (2 * q) ** 2 * 4 if model == 1 else 0
-    return n * (1 + 2 + 4) + tiles * (1024 + 256 * 5 + 4 + 16) + ring + table + 4096
+    return n * (1 + 2 + 4) + tiles * (1024 + 256 * 4 + 4 + 16) + ring + table + 4096
 
 
 class GpuBackend:
