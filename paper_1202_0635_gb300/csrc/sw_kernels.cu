@@ -42,6 +42,7 @@ constexpr int kEnergyThreads = 256;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kInfLabel = 1 << 20;      // "no label" (larger than any tile node)
 constexpr int kMaxPairs = 1024;         // queued unions per tile (more are joined at once)
+constexpr int kWarpPairs = kMaxPairs / kTaskWarps;   // each warp queues into its own segment
 constexpr int kFreshList = 2 * kMaxPairs;  // fresh labels listed per tile (more: settled in place)
 // Resolved root word: kTileResolved | kResClosed | state (or kResFlip), or
 // kTileResolved | open slot.
@@ -52,6 +53,7 @@ static_assert(QW == 32, "a warp quadrant is 32 x 32: lane r owns row r as a 32-b
 static_assert(TW == 2 * QW && TH == 2 * QW, "a tile is 2 x 2 quadrants");
 static_assert(sizeof(Lattice) % 8 == 0, "lattice descriptors are copied in 8-byte words");
 static_assert(TW == 64 && kBlockThreads == NS / 32, "lane = column pair; thread t owns labels 32 t .. 32 t + 31");
+static_assert(kTaskWarps == 4, "one union queue per quadrant warp, four segments");
 
 __device__ __forceinline__ unsigned long long read_u64(const unsigned long long *p)
 {
@@ -109,7 +111,7 @@ __device__ __forceinline__ int byte_at(const uint32_t (&w)[8], int c)
 __device__ __forceinline__ void queue_union(uint32_t *pairs, int idx, int a, int b, volatile uint16_t *par,
                                             DevState *st, int where)
 {
-    if (idx < kMaxPairs) pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
+    if (idx < kWarpPairs) pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
     else if (!union_t(par, a, b, kTileSites + 1)) record_error(st, kErrUnionCap, where);
 }
 
@@ -190,59 +192,85 @@ __device__ __forceinline__ void load_partners(const int8_t *spin, int L, int y, 
 #pragma unroll
     for (int k = 0; k < 8; ++k) px[k] = py[k] = 0u;
     if (!rv) return;
-    const int yr = (y + r) % L;
+    const int yr = y + r < L ? y + r : y + r - L;   // 0 < r < L
     const uint32_t *prow = reinterpret_cast<const uint32_t *>(spin + (size_t)yr * L + x0);
+    const bool whole = (L & 15) == 0 && ncols == 32;   // 16-byte aligned half rows
+    if (whole) {
+        const uint4 a0 = __ldg(reinterpret_cast<const uint4 *>(prow)), a1 = __ldg(reinterpret_cast<const uint4 *>(prow) + 1);
+        py[0] = a0.x; py[1] = a0.y; py[2] = a0.z; py[3] = a0.w;
+        py[4] = a1.x; py[5] = a1.y; py[6] = a1.z; py[7] = a1.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) py[k] = (4 * k < ncols) ? __ldg(prow + k) : 0u;
-    const int cx = (x0 + r) % L;
-    if ((cx & 3) == 0 && cx + ncols <= L) {   // word aligned, no wrap
-        const uint32_t *xrow = reinterpret_cast<const uint32_t *>(spin + (size_t)y * L + cx);
+        for (int k = 0; k < 8; ++k) py[k] = (4 * k < ncols) ? __ldg(prow + k) : 0u;
+    }
+    const int cx = x0 + r < L ? x0 + r : x0 + r - L;
+    const uint32_t *xrow = reinterpret_cast<const uint32_t *>(spin + (size_t)y * L + cx);
+    if (whole && (cx & 15) == 0 && cx + ncols <= L) {
+        const uint4 a0 = __ldg(reinterpret_cast<const uint4 *>(xrow)), a1 = __ldg(reinterpret_cast<const uint4 *>(xrow) + 1);
+        px[0] = a0.x; px[1] = a0.y; px[2] = a0.z; px[3] = a0.w;
+        px[4] = a1.x; px[5] = a1.y; px[6] = a1.z; px[7] = a1.w;
+    } else if ((cx & 3) == 0 && cx + ncols <= L) {   // word aligned, no wrap
 #pragma unroll
         for (int k = 0; k < 8; ++k) px[k] = (4 * k < ncols) ? __ldg(xrow + k) : 0u;
-    } else {
-        for (int j = 0; j < ncols; ++j) {
-            const uint32_t b = (uint8_t)__ldg(spin + (size_t)y * L + (x0 + j + r) % L);
+    } else {   // unrolled: px stays in registers
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j >= ncols) break;
+            const int xj = cx + j < L ? cx + j : cx + j - L;
+            const uint32_t b = (uint8_t)__ldg(spin + (size_t)y * L + xj);
             px[j >> 2] |= b << (8 * (j & 3));
         }
     }
 }
 
-// Clock classes min(dk, q - dk) of four state pairs at once (the bytes of
-// a and b; q <= 15, so every class is below 8); a state outside [0, q)
-// counts as state 0.
-__device__ __forceinline__ uint32_t clock_classes4(uint32_t a, uint32_t b, uint32_t q4)
+// Bytes of x outside [0, q) set to state 0 (q <= 15): a byte is out of
+// range if its top bit is set or its low seven bits reach q.
+__device__ __forceinline__ uint32_t clock_valid4(uint32_t x, uint32_t q4)
 {
-    a &= __vcmpltu4(a, q4);
-    b &= __vcmpltu4(b, q4);
-    uint32_t d = __vsub4(__vadd4(a, q4), b);   // a - b + q, in [1, 2q - 1]
-    d = __vsub4(d, __vcmpgeu4(d, q4) & q4);     // (a - b) mod q
-    return __vminu4(d, __vsub4(q4, d));
+    const uint32_t big = (((x & 0x7F7F7F7Fu) + (0x80808080u - q4)) | x) & 0x80808080u;
+    return x & ~((big >> 7) * 0xFFu);
 }
 
-// Tally of pair classes below 8, four pairs (bytes) at a time: how many
-// pairs have each combination of class bits set (bit planes), from which
-// the count of every class follows by inclusion-exclusion.
+// Clock classes min(dk, q - dk), dk = (a - b) mod q, of four state pairs at
+// once: the bytes of a and b, states in [0, q), q <= 15 (every class is
+// below 8).  Each byte lane works on 128 + value so that no lane borrows
+// from its neighbour.
+__device__ __forceinline__ uint32_t clock_classes4(uint32_t a, uint32_t b, uint32_t q4)
+{
+    uint32_t d = (a | 0x80808080u) - b;                              // 128 + a - b
+    d += ((~d >> 7) & 0x01010101u) * (q4 & 0xFFu);                    // + q where a < b
+    const uint32_t e = d & 0x7F7F7F7Fu;                              // dk
+    const uint32_t f = q4 - e;                                       // q - dk, in [1, q]
+    const uint32_t ge = ((((e | 0x80808080u) - f) & 0x80808080u) >> 7) * 0xFFu;   // dk >= q - dk
+    return e ^ ((e ^ f) & ge);
+}
+
+// Tally of pair classes below 2^BITS, four pairs (bytes) at a time: how
+// many pairs have each combination of class bits set (bit planes), from
+// which the count of every class follows by inclusion-exclusion.
+template <int BITS>
 struct ClassTally {
-    unsigned n = 0;                              // pairs
-    unsigned m[7] = {0, 0, 0, 0, 0, 0, 0};      // m[S - 1]: pairs whose class has all bits of S (S = 1..7)
+    static constexpr int kSets = (1 << BITS) - 1;
+    unsigned n = 0;           // pairs
+    unsigned m[kSets] = {};   // m[S - 1]: pairs whose class has all bits of S (S = 1 .. 2^BITS - 1)
     __device__ __forceinline__ void add4(uint32_t cls)
     {
-        const uint32_t b0 = cls & 0x01010101u, b1 = (cls >> 1) & 0x01010101u, b2 = (cls >> 2) & 0x01010101u;
         n += 4u;
-        m[0] += __popc(b0);
-        m[1] += __popc(b1);
-        m[2] += __popc(b0 & b1);
-        m[3] += __popc(b2);
-        m[4] += __popc(b0 & b2);
-        m[5] += __popc(b1 & b2);
-        m[6] += __popc(b0 & b1 & b2);
+#pragma unroll
+        for (int S = 1; S <= kSets; ++S) {
+            uint32_t b = 0x01010101u;
+#pragma unroll
+            for (int j = 0; j < BITS; ++j)
+                if ((S >> j) & 1) b &= cls >> j;
+            m[S - 1] += __popc(b);
+        }
     }
     // Pairs of class d: sum over S containing d of (-1)^|S - d| N_S.
     __device__ __forceinline__ unsigned count(int d) const
     {
         int c = 0;
 #pragma unroll
-        for (int S = 0; S < 8; ++S) {
+        for (int S = 0; S <= kSets; ++S) {
             if ((S & d) != d) continue;
             const int ns = S ? (int)m[S - 1] : (int)n;
             c += (__popc(S ^ d) & 1) ? -ns : ns;
@@ -253,37 +281,74 @@ struct ClassTally {
     __device__ __forceinline__ void flush(unsigned int *hist, int nclass) const
     {
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
+        for (int d = 0; d <= kSets; ++d) {
             const unsigned int v = __reduce_add_sync(FULL, count(d));
             if ((threadIdx.x & 31) == 0 && v && d < nclass) atomicAdd(&hist[d], v);
         }
     }
 };
 
-// Clock classes min(dk, q - dk) of the pairs (row byte c, px byte c) and
-// (row byte c, py byte c), c < ncols, into a shared histogram.  Must be
-// called by all 32 lanes of the warp.
-__device__ __forceinline__ void count_pair_classes(unsigned int *hist, const uint32_t (&wd)[8], const uint32_t (&px)[8],
-                                                   const uint32_t (&py)[8], int ncols, bool rv, int q, int nclass)
+// Clock classes of the pairs (row byte c, px byte c) and (row byte c, py
+// byte c), c < ncols, into a shared histogram; the row words hold valid
+// states, q <= 15.  All 32 lanes of the warp.
+template <int BITS>
+__device__ __forceinline__ void tally_pairs(unsigned int *hist, const uint32_t (&wd)[8], const uint32_t (&px)[8],
+                                            const uint32_t (&py)[8], int ncols, bool rv, uint32_t q4, int nclass)
 {
-    if (nclass <= 8) {   // q <= 15: four pairs per word
-        const uint32_t q4 = (uint32_t)q * 0x01010101u;
-        ClassTally t;
+    ClassTally<BITS> t;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!(rv && 4 * k < ncols)) continue;   // ncols % 4 == 0
+        t.add4(clock_classes4(wd[k], clock_valid4(px[k], q4), q4));
+        t.add4(clock_classes4(wd[k], clock_valid4(py[k], q4), q4));
+    }
+    t.flush(hist, nclass);
+}
+
+// The same for any q, one pair at a time.
+__device__ __forceinline__ void tally_pairs_any(unsigned int *hist, const uint32_t (&wd)[8], const uint32_t (&px)[8],
+                                                const uint32_t (&py)[8], int ncols, bool rv, int q)
+{
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const bool v = rv && c < ncols;
+        const int s0 = byte_at(wd, c);
+        add_hist_any(hist, clock_bond_class(s0, byte_at(px, c), q), v);
+        add_hist_any(hist, clock_bond_class(s0, byte_at(py, c), q), v);
+    }
+}
+
+// Clock classes of the incoming configuration seen from one half row of
+// k_bonds, q <= 15 (classes below 2^BITS): the nearest-neighbour pairs
+// (right, down) into hist_class, and the pairs at distance L/4 and L/2
+// (Sec. 4, G(r,T)) into hist4 and hist2.  wd, dn and sr are the row, the
+// row below and the state right of the row; wd is sanitised in place (the
+// bonds are drawn by then).  All 32 lanes of the warp.
+template <int BITS>
+__device__ __forceinline__ void clock_row_classes(unsigned int *hist_class, unsigned int *hist4, unsigned int *hist2,
+                                                  const int8_t *spin, int L, int y, int x0, int ncols, bool rv, int q,
+                                                  int nclass, uint32_t (&wd)[8], const uint32_t (&dn)[8], uint32_t sr)
+{
+    const uint32_t q4 = (uint32_t)q * 0x01010101u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) wd[k] = clock_valid4(wd[k], q4);
+    sr = (uint32_t)valid_state((int)sr, q);
+    {
+        ClassTally<BITS> t;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             if (!(rv && 4 * k < ncols)) continue;   // ncols % 4 == 0
-            t.add4(clock_classes4(wd[k], px[k], q4));
-            t.add4(clock_classes4(wd[k], py[k], q4));
+            const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
+            t.add4(clock_classes4(wd[k], __funnelshift_r(wd[k], nxt, 8), q4));
+            t.add4(clock_classes4(wd[k], clock_valid4(dn[k], q4), q4));
         }
-        t.flush(hist, nclass);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const bool v = rv && c < ncols;
-            const int s0 = byte_at(wd, c);
-            add_hist_any(hist, clock_bond_class(s0, byte_at(px, c), q), v);
-            add_hist_any(hist, clock_bond_class(s0, byte_at(py, c), q), v);
-        }
+        t.flush(hist_class, nclass);
+    }
+#pragma unroll 1
+    for (int w = 0; w < 2; ++w) {
+        uint32_t px[8], py[8];
+        load_partners(spin, L, y, x0, w == 0 ? L / 4 : L / 2, ncols, rv, px, py);
+        tally_pairs<BITS>(w == 0 ? hist4 : hist2, wd, px, py, ncols, rv, q4, nclass);
     }
 }
 
@@ -457,19 +522,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                     }
                 } else if (!CLOCK_MEASURE) {
                     record_error(lat.st, kErrInternal, 0);   // a clock lattice needs the clock variant
-                } else if (lat.nclass <= 8) {
-                    // q <= 15: the classes of four pairs per word, tallied by
-                    // bit planes and reduced over the warp once per tile.
-                    const uint32_t q4 = (uint32_t)q * 0x01010101u;
-                    ClassTally tl;
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (!(rv && 4 * k < ncols)) continue;   // ncols % 4 == 0
-                        const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
-                        tl.add4(clock_classes4(wd[k], __funnelshift_r(wd[k], nxt, 8), q4));
-                        tl.add4(clock_classes4(wd[k], dn[k], q4));
-                    }
-                    tl.flush(hist_class, lat.nclass);
+                } else if (lat.nclass <= 4) {
+                    // q <= 7: classes in two bits, four pairs per word,
+                    // tallied by bit planes and reduced over the warp.
+                    clock_row_classes<2>(hist_class, hist_corr[0], hist_corr[1], lat.spin, L, y, x0, ncols, rv, q,
+                                         lat.nclass, wd, dn, sr);
+                } else if (lat.nclass <= 8) {   // q <= 15: three bits
+                    clock_row_classes<3>(hist_class, hist_corr[0], hist_corr[1], lat.spin, L, y, x0, ncols, rv, q,
+                                         lat.nclass, wd, dn, sr);
                 } else {
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
@@ -479,16 +539,12 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                         add_hist_any(hist_class, clock_bond_class(s0, s1, q), v);
                         add_hist_any(hist_class, clock_bond_class(s0, byte_at(dn, c), q), v);
                     }
-                }
-                if (CLOCK_MEASURE && clock) {
-                    // Correlation pairs (i, i + r x), (i, i + r y) at r = L/4 and
-                    // r = L/2 (Sec. 4, G(r,T)) of the incoming configuration.
+                    // Correlation pairs at r = L/4 and r = L/2 (Sec. 4, G(r,T)).
 #pragma unroll 1
                     for (int w = 0; w < 2; ++w) {
-                        const int r = w == 0 ? L / 4 : L / 2;
                         uint32_t px[8], py[8];
-                        load_partners(lat.spin, L, y, x0, r, ncols, rv, px, py);
-                        count_pair_classes(hist_corr[w], wd, px, py, ncols, rv, q, lat.nclass);
+                        load_partners(lat.spin, L, y, x0, w == 0 ? L / 4 : L / 2, ncols, rv, px, py);
+                        tally_pairs_any(hist_corr[w], wd, px, py, ncols, rv, q);
                     }
                 }
             }
@@ -518,7 +574,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
     __shared__ __align__(8) unsigned int rowR[TH][2], rowD[TH][2];
     __shared__ unsigned int openw[NS / 32];
     __shared__ int rmin_all[kTaskWarps][QW];                // per-warp run minima of the scan
-    __shared__ int s_nopen, s_npairs, s_wsum[kTaskWarps];
+    __shared__ int s_nopen, s_npairs[kTaskWarps], s_wsum[kTaskWarps];
     __shared__ unsigned int s_cross[kCrossWords];
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
@@ -565,7 +621,8 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         unsigned Rq = 0, Dq = 0;   // lane r: row r's bonds inside the quadrant (right, down)
 
         for (int i = threadIdx.x; i < NS / 32; i += blockDim.x) openw[i] = 0u;
-        if (threadIdx.x == 0) s_nopen = s_npairs = 0;
+        if (threadIdx.x == 0) s_nopen = 0;
+        if (threadIdx.x < kTaskWarps) s_npairs[threadIdx.x] = 0;
 
         // ===== bond masks of my quadrant (written by k_bonds), lane = row ======
         if (qa) {
@@ -612,6 +669,8 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
             const unsigned lanes_lt = bit - 1u;
             const int nb = (QW * qy) * TW + QW * qx;  // node of the quadrant's corner
             int *rmin = rmin_all[warp];
+            uint32_t *wq = upairs + warp * kWarpPairs;   // this warp's union queue
+            int nq = 0;                               // pairs queued so far (warp-uniform)
             int pl = 0;                               // label of the site above (valid where Dp has my bit)
             uint32_t lastq = 0xFFFFFFFFu;             // pair this lane queued last
             unsigned Dp = 0u, Rp = 0u;
@@ -641,30 +700,44 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                 const bool u = (E & bit) && pl != mlab && pair != lastq;
                 const unsigned bu = __ballot_sync(FULL, u);
                 if (bu) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&s_npairs, __popc(bu));
-                    base = __shfl_sync(FULL, base, 0);
+                    if (nq + __popc(bu) > kWarpPairs) __syncwarp();   // full: joined at once, after this row's stores
                     if (u) {
-                        queue_union(upairs, base + __popc(bu & lanes_lt), pl, mlab, par, lat.st, Y0 * L + X0);
+                        queue_union(wq, nq + __popc(bu & lanes_lt), pl, mlab, par, lat.st, Y0 * L + X0);
                         lastq = pair;
                     }
+                    nq += __popc(bu);
                 }
                 __syncwarp();
                 pl = mlab;
                 Rp = Rr;
                 Dp = __shfl_sync(FULL, Dq, row);
             }
+            if (lane == 0) s_npairs[warp] = min(nq, kWarpPairs);
         }
         __syncthreads();
 
         // ===== unions: queued pairs, then the seams between the quadrants =====
         {
-            const int np = min(s_npairs, kMaxPairs);
+            const int n0 = s_npairs[0], n1 = s_npairs[1], n2 = s_npairs[2], n3 = s_npairs[3];
+            const int np = n0 + n1 + n2 + n3;
             const int nitems = np + TH + TW;
             for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
                 int a, c;
-                if (i < np) {
-                    const uint32_t pr = upairs[i];
+                if (i < np) {   // item i -> segment w, entry k
+                    int k = i, w = 0;
+                    if (k >= n0) {
+                        k -= n0;
+                        w = 1;
+                        if (k >= n1) {
+                            k -= n1;
+                            w = 2;
+                            if (k >= n2) {
+                                k -= n2;
+                                w = 3;
+                            }
+                        }
+                    }
+                    const uint32_t pr = upairs[w * kWarpPairs + k];
                     a = (int)(pr & 0xFFFFu);
                     c = (int)(pr >> 16);
                 } else if (i < np + TH) {   // column 31 - 32 of row y

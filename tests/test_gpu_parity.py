@@ -38,8 +38,11 @@ def make_pair(L, q, model, T, seed, init):
     return g, o
 
 
-def run_lockstep(L, q, model, T, seed, init, n, graph=False, labels=True, every=1):
+def run_lockstep(L, q, model, T, seed, init, n, graph=False, labels=True, every=1, spins=None):
     g, o = make_pair(L, q, model, T, seed, init)
+    if spins is not None:
+        g.spins = spins
+        o.spins = spins
     assert np.array_equal(g.spins, o.spins), "initial spins"
     sw.sw_set_graph(g.h, graph)
     sw.sw_set_debug_labels(g.h, labels)
@@ -101,6 +104,32 @@ def test_clock(L, q, T):
 def test_potts_extremes(q, T):
     """Frozen (T -> 0: one cluster), infinite T (no bonds), q = 127."""
     run_lockstep(64, q, POTTS, T, 5, "random", 12)
+
+
+def stripes32():
+    """A 32 x 32 Potts colouring (q >= 3) on which, with every equal pair
+    bonded (T -> 0), each even row is one run joining the 16 separate
+    single-site runs of the row above: 15 union requests per even row,
+    225 per 32 x 32 block, the most found by a search over colourings."""
+    s = np.empty((32, 32), np.int8)
+    s[0] = 2
+    for r in range(1, 32):
+        m = ((r - 1) // 2) % 2
+        if r % 2:
+            s[r, 0::2] = m
+            s[r, 1::2] = 2 if r == 1 else 1 - m
+        else:
+            s[r] = m
+    return s
+
+
+@pytest.mark.parametrize("L", [128, 200])
+def test_union_heavy_colouring(L):
+    """Every 32 x 32 block of the lattice (the warp quadrants of the tile
+    labeling) carries the stripe colouring: the heaviest union load."""
+    reps = (L + 31) // 32
+    spins = np.tile(stripes32(), (reps, reps))[:L, :L]
+    run_lockstep(L, 3, POTTS, 1e-3, 4, "random", 3, spins=spins)
 
 
 def test_graph_mode_matches_direct_launches():
