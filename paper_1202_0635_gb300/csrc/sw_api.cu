@@ -145,7 +145,7 @@ struct sw_handle {
 
     int ntiles() const { return tiles_x * tiles_y; }
     int ntasks() const { return ntiles(); }
-    long long nmerge() const { return (long long)L * (tiles_x + tiles_y); }
+    long long nmerge() const { return (long long)ntiles() * swgb::kMergeItems; }
 
     Batch self_batch() const
     {
@@ -1446,7 +1446,7 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
         lat.thr_tab = (const uint32_t *)(base + kNoalloc.thr_tab);
     }
     const int task_off[2] = {0, tiles_x * tiles_y};
-    const long long merge_off[2] = {0, (long long)L * (tiles_x + tiles_y)};
+    const long long merge_off[2] = {0, (long long)tiles_x * tiles_y * swgb::kMergeItems};
     Batch b{};
     b.lat = (const Lattice *)(base + kNoalloc.lat);
     b.task_off = (const int *)(base + kNoalloc.task_off);

@@ -59,7 +59,7 @@ constexpr int kTaskWarps = 4;
 struct Batch {
     const Lattice *lat;            // [nrep] descriptors (device memory)
     const int *task_off;           // [nrep + 1] prefix sums of the lattices' tile counts
-    const long long *merge_off;    // [nrep + 1] prefix sums of L * (tiles_x + tiles_y)
+    const long long *merge_off;    // [nrep + 1] prefix sums of the lattices' merge items (kMergeItems a tile)
     unsigned int *ticket;          // blocks finished in the sweep's last kernel
     int nrep;
     int ntasks;
@@ -146,8 +146,10 @@ __device__ __forceinline__ void union_roots(int32_t *label, int a, int b, int ca
 {
     const long long t0 = clock64();
     for (int it = 0; it < cap; ++it) {
-        a = find_root_halving(label, a, cap, st);
-        b = find_root_halving(label, b, cap, st);
+        // Both parents in flight at once: most ends are roots already.
+        const int pa = ld_volatile(label + a), pb = ld_volatile(label + b);
+        if (pa != a) a = find_root_halving(label, pa, cap, st);
+        if (pb != b) b = find_root_halving(label, pb, cap, st);
         if (a == b) return;
         const int hi = a > b ? a : b;
         const int lo = a > b ? b : a;

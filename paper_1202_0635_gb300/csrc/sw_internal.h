@@ -25,9 +25,14 @@ constexpr int kOpenSlots = 256;
 // Crossing-bond words per tile: [0], [1] bit r = right-edge bond of row
 // 32 * w + r; [2], [3] bit c = bottom-edge bond of column 32 * w + c.
 constexpr int kCrossWords = 4;
-// Per-site code: closed component -> kCodeClosed | new state; open
-// component -> slot of its root in the tile's open list.
-constexpr uint16_t kCodeClosed = 0x8000;
+// Merge items per tile: the 64 rows of its right edge, then the 64
+// columns of its bottom edge.
+constexpr int kMergeItems = 128;
+// Per-site code: closed component -> kCodeClosed | new state (below 128);
+// open component -> slot of its root in the tile's open list (below 256).
+// A Potts code thus indexes one table: the open slots' new states, then
+// entry kCodeClosed + s = s.
+constexpr uint16_t kCodeClosed = 0x100;
 
 // Bond-mask words per tile (right and down bonds of 64 rows, 2 words a row).
 constexpr int kBondWords = 2 * kTileH * (kTileW / 32);

@@ -946,29 +946,29 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
 
 // ---------------------------------------------------------------------------
 // k_merge: union of the open roots across every active crossing bond.
-// Work items of a lattice: L * tiles_x right-edge bonds, then L * tiles_y
-// bottom-edge bonds.
+// Work items of a lattice: kMergeItems per tile, the 64 rows of its right
+// edge, then the 64 columns of its bottom edge; a warp takes 32
+// consecutive items (one side of one tile).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int open_root_of(const Lattice &lat, int site, bool &ok)
+__device__ __forceinline__ int open_root_of(const Lattice &lat, int site, int tile, bool &ok)
 {
-    const int sy = site / lat.L, sx = site - sy * lat.L;
     const int code = lat.code[site];   // open site: slot of its root in the tile's open list
     if (code & kCodeClosed) {
         ok = false;
         return site;
     }
-    const int tile = (sy / TH) * lat.tiles_x + sx / TW;
     return __ldg(lat.open_list + (size_t)tile * kOpenSlots + code);
 }
 
 __global__ void k_merge(Batch b)
 {
+    static_assert(kMergeItems == TH + TW, "merge items: right edge rows, then bottom edge columns");
     long long lo = 0, hi = 0;
     int rep = -1;
     Lattice lat;
     const unsigned lane = threadIdx.x & 31;
-    // Warp-uniform trip count: the lanes of a warp take consecutive items,
-    // so neighbouring bonds of one tile edge meet in one warp.
+    // Every lattice has a multiple of kMergeItems items: a warp never spans
+    // two lattices, and its trip count is uniform.
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < b.nmerge;
          base += (long long)gridDim.x * blockDim.x) {
         const long long k = base + lane;
@@ -981,30 +981,32 @@ __global__ void k_merge(Batch b)
                 hi = __ldg(b.merge_off + rep + 1);
                 lat = b.lat[rep];
             }
-            const int L = lat.L, ncol = lat.tiles_x;
-            const long long kk = k - lo;
-            const long long nright = (long long)L * ncol;
-            int i, j;
-            if (kk < nright) {   // right edge of tile column c, row y (rows run fastest)
-                const int c = (int)(kk / L), y = (int)(kk % L);
-                const int tile = (y / TH) * ncol + c;
-                ok = (__ldg(lat.cross + (size_t)tile * kCrossWords + ((y % TH) >> 5)) >> (y & 31)) & 1u;
-                const int x = min((c + 1) * TW, L) - 1;
+            const int L = lat.L;
+            const int kk = (int)(k - lo);
+            const int tile = kk / kMergeItems, e = kk % kMergeItems;
+            const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
+            const int X0 = bx * TW, Y0 = by * TH;
+            const int tw = min(TW, L - X0), th = min(TH, L - Y0);
+            const uint32_t *cw = lat.cross + (size_t)tile * kCrossWords;
+            int i, j, nt;
+            if (e < TH) {   // right edge, row e, into the next tile to the right
+                ok = e < th && ((__ldg(cw + (e >> 5)) >> (e & 31)) & 1u);
+                const int y = Y0 + e, x = X0 + tw - 1;
                 i = y * L + x;
                 j = y * L + (x + 1 == L ? 0 : x + 1);
-            } else {             // bottom edge of tile row rr, column x
-                const long long k2 = kk - nright;
-                const int rr = (int)(k2 / L), x = (int)(k2 % L);
-                const int tile = rr * ncol + x / TW;
-                ok = (__ldg(lat.cross + (size_t)tile * kCrossWords + 2 + ((x % TW) >> 5)) >> (x & 31)) & 1u;
-                const int y = min((rr + 1) * TH, L) - 1;
+                nt = by * lat.tiles_x + (bx + 1 == lat.tiles_x ? 0 : bx + 1);
+            } else {        // bottom edge, column e - 64, into the next tile below
+                const int c = e - TH;
+                ok = c < tw && ((__ldg(cw + 2 + (c >> 5)) >> (c & 31)) & 1u);
+                const int x = X0 + c, y = Y0 + th - 1;
                 i = y * L + x;
                 j = (y + 1 == L ? 0 : y + 1) * L + x;
+                nt = (by + 1 == lat.tiles_y ? 0 : by + 1) * lat.tiles_x + bx;
             }
             if (ok) {
                 bool open = true;
-                a = open_root_of(lat, i, open);
-                c2 = open_root_of(lat, j, open);
+                a = open_root_of(lat, i, tile, open);
+                c2 = open_root_of(lat, j, nt, open);
                 if (!open) {   // a crossing bond always ends at open sites
                     record_error(lat.st, kErrInternal, i);
                     ok = false;
@@ -1015,7 +1017,7 @@ __global__ void k_merge(Batch b)
         const unsigned vm = __ballot_sync(0xffffffffu, ok);
         if (ok) {
             const unsigned long long key = ((unsigned long long)(unsigned)a << 32) | (unsigned)c2;
-            const unsigned peers = __match_any_sync(vm, key) & __match_any_sync(vm, rep);
+            const unsigned peers = __match_any_sync(vm, key);
             if ((unsigned)__ffs(peers) - 1u == lane) union_roots(lat.label, a, c2, lat.L * lat.L + 1, lat.st);
         }
     }
@@ -1058,7 +1060,9 @@ __device__ void finish_sweep(const Batch &b)
 template <bool MEASURE, bool LABELS>
 __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
 {
-    __shared__ __align__(16) unsigned char tab[kOpenSlots];
+    // New state (Potts) or reflection flag (clock) of each open slot; then
+    // entry kCodeClosed + s = s, so that a Potts code indexes its new state.
+    __shared__ __align__(16) unsigned char tab[kOpenSlots + SW_MAX_Q];
     __shared__ int rootg[LABELS ? kOpenSlots : 1];
     __shared__ unsigned int hist_state[SW_MAX_Q + 1];
     __shared__ unsigned int red[32];
@@ -1072,6 +1076,8 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
     unsigned long long cnt_lo = 0, cnt_hi = 0;
     unsigned int open_roots = 0;   // clusters reaching a tile border, counted at their root
     int cur = -1;
+    static_assert(kCodeClosed == kOpenSlots && SW_MAX_Q <= 128, "codes index the table");
+    for (int k = threadIdx.x; k < SW_MAX_Q; k += blockDim.x) tab[kOpenSlots + k] = (unsigned char)k;
     auto flush = [&]() {
         if (MEASURE && cur >= 0) {
             block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass + 1, open_roots, red);
@@ -1160,13 +1166,12 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const uint32_t code = ((h < 2) ? (cw[k].x >> (16 * h)) : (cw[k].y >> (16 * (h - 2)))) & 0xFFFFu;
-                const int open_state = tab[code & 0xFFu];   // meaningful for open sites only
                 int ns;
                 if (clock) {
                     const int k0 = valid_state((int)((sw[k] >> (8 * h)) & 0xFFu), q);
-                    ns = (code & kCodeClosed) ? (int)(code & 0x7Fu) : (open_state ? reflect(k0, m, q) : k0);
+                    ns = (code & kCodeClosed) ? (int)(code & 0x7Fu) : (tab[code & 0xFFu] ? reflect(k0, m, q) : k0);
                 } else {
-                    ns = (code & kCodeClosed) ? (int)(code & 0x7Fu) : open_state;
+                    ns = tab[min(code, (uint32_t)(kOpenSlots + SW_MAX_Q - 1))];   // open slot or kCodeClosed | state
                 }
                 if (MEASURE && q > 2 && q <= 8) {
                     const unsigned long long one = 1ull << (16 * (ns & 3));
