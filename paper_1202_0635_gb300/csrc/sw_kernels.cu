@@ -1057,7 +1057,7 @@ __device__ void finish_sweep(const Batch &b)
 // components, all spin writes, state counts.  One block per tile, one warp
 // per quadrant.
 // ---------------------------------------------------------------------------
-template <bool MEASURE, bool LABELS>
+template <bool MEASURE, bool LABELS, bool ANY_CLOCK>
 __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
 {
     // New state (Potts) or reflection flag (clock) of each open slot; then
@@ -1118,7 +1118,8 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
         }
         const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
-        const bool clock = lat.clock != 0;
+        const bool clock = ANY_CLOCK && lat.clock != 0;   // ANY_CLOCK: the batch holds a clock lattice
+        if (!ANY_CLOCK && lat.clock && threadIdx.x == 0) record_error(lat.st, kErrInternal, 0);
         const int m = ctx.m;
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int X0 = bx * TW, Y0 = by * TH;
@@ -1144,10 +1145,13 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
         // tile's table.  A cluster is counted once, by the tile holding its root.
         {
             const size_t k0 = (size_t)tile * kOpenSlots;
-            const int n = lat.open_count[tile];
+            // Slot threadIdx.x is read before the count arrives (the list
+            // has kOpenSlots entries; those beyond the count are not used).
+            const int r0 = __ldg(lat.open_list + k0 + threadIdx.x);
+            const int n = __ldg(lat.open_count + tile);
             const int cap = L * L + 1;
             for (int s = threadIdx.x; s < n; s += blockDim.x) {
-                const int r = lat.open_list[k0 + s];
+                const int r = s == (int)threadIdx.x ? r0 : __ldg(lat.open_list + k0 + s);
                 const int root = find_root_halving(lat.label, r, cap, lat.st);
                 if (MEASURE && root == r) ++open_roots;
                 const uint32_t u = draw4(lat, (uint32_t)root, ctx.t, kTagState).x;
@@ -1320,7 +1324,11 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
         (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * shape.merge));
     k_merge<<<mblocks, 256, 0, s>>>(b);
     mark();
-    k_flip_tiles<MEASURE, LABELS><<<std::max(1, std::min(b.ntasks, sm_count * shape.flip)), kBlockThreads, 0, s>>>(b);
+    const int fblocks = std::max(1, std::min(b.ntasks, sm_count * shape.flip));
+    if (b.any_clock)
+        k_flip_tiles<MEASURE, LABELS, true><<<fblocks, kBlockThreads, 0, s>>>(b);
+    else
+        k_flip_tiles<MEASURE, LABELS, false><<<fblocks, kBlockThreads, 0, s>>>(b);
     mark();
     return cudaGetLastError();
 }
