@@ -227,8 +227,10 @@ __device__ __forceinline__ int link_t(volatile uint16_t *par, int hi, int lo)
 __device__ __forceinline__ bool union_t(volatile uint16_t *par, int a, int b, int cap)
 {
     for (int it = 0; it < cap; ++it) {
-        a = find_t(par, a, cap);
-        b = find_t(par, b, cap);
+        // Both parents in flight at once: the ends are often roots.
+        const int pa = par_ld(par, a), pb = par_ld(par, b);
+        if (pa != a) a = find_t(par, pa, cap);
+        if (pb != b) b = find_t(par, pb, cap);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
         const int hi = a > b ? a : b;
