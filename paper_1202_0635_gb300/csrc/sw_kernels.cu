@@ -1058,7 +1058,7 @@ __device__ void finish_sweep(const Batch &b)
 // per quadrant.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS, bool ANY_CLOCK>
-__global__ void __launch_bounds__(kBlockThreads, 8) k_flip_tiles(Batch b)
+__global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? 8 : 10) k_flip_tiles(Batch b)   // Potts: 10 blocks / SM
 {
     // New state (Potts) or reflection flag (clock) of each open slot; then
     // entry kCodeClosed + s = s, so that a Potts code indexes its new state.
