@@ -1,8 +1,10 @@
 """Temperature scans on the GPU engine (Komura & Okabe, arXiv:1202.0635,
 Sec. 4): the moment ratio U(T) = <M^4>/<M^2>^2 of several sizes (Eq. U; the
 crossing of the curves marks the critical point, Fig. 4), the time per spin
-flip against T with its per-stage split (Figs. 3 and 5), and the
-correlation ratio R(T) = G(L/2)/G(L/4) of the clock model (Fig. 6).
+flip against T with its per-stage split (Figs. 3 and 5), the correlation
+ratio R(T) = G(L/2)/G(L/4) of the clock model (Fig. 6), and the time per
+spin flip over the paper's grid of models and sizes, with and without the
+measurement (the two rows of its timing tables).
 
 Every (L, T) point is its own lattice; all of them advance together in one
 batch (one launch sequence per sweep), so a scan costs about as much as
@@ -91,6 +93,50 @@ def timing(q, model, L, temps, sweeps=20, equil=50, seed=1):
     return out
 
 
+def sweep_time(L, q, model, T, measure, sweeps=200, equil=100, seed=1):
+    """Device time per spin flip (ns) of graph-launched sweeps of one
+    lattice: CUDA events on the lattice's stream around `sweeps` sweeps,
+    after `equil` sweeps from a random start."""
+    import torch
+    sw = _sw()
+    s = torch.cuda.Stream()
+    lat = sw.Lattice(L, q, model, T, seed, init=sw.SW_INIT_RANDOM, stream=s.cuda_stream)
+    try:
+        sw.sw_set_measure(lat.h, measure)
+        sw.sw_set_graph(lat.h, 1)
+        lat.sweep(equil)
+        sw.sw_synchronize(lat.h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        lat.sweep(sweeps)
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e6 / sweeps / (L * L)
+    finally:
+        lat.close()
+
+
+def timing_matrix(sizes=(1024, 2048, 4096), sweeps=200, equil=100):
+    """ns per spin flip, update only and with measurement: Potts q = 2, 3, 4
+    at T_c for each size, and the q = 6 clock model at L = max(sizes) and
+    T = 0.7, 0.9, 1.2 (below, at and above the upper KT temperature)."""
+    sw = _sw()
+    rows = []
+    for q in (2, 3, 4):
+        T = workloads.critical_temperature(q, sw.SW_POTTS)
+        for L in sizes:
+            rows.append({"model": "potts", "q": q, "L": L, "T": T,
+                         "update_only": sweep_time(L, q, sw.SW_POTTS, T, 0, sweeps, equil),
+                         "with_measurement": sweep_time(L, q, sw.SW_POTTS, T, 1, sweeps, equil)})
+    L = max(sizes)
+    for T in (0.7, 0.9, 1.2):
+        rows.append({"model": "clock", "q": 6, "L": L, "T": T,
+                     "update_only": sweep_time(L, 6, sw.SW_CLOCK, T, 0, sweeps, equil),
+                     "with_measurement": sweep_time(L, 6, sw.SW_CLOCK, T, 1, sweeps, equil)})
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--q", type=int, default=2)
@@ -102,9 +148,13 @@ def main():
     ap.add_argument("--hi", type=float, default=1.1)
     ap.add_argument("--n", type=int, default=9)
     ap.add_argument("--timing-L", type=int, default=1024)
+    ap.add_argument("--matrix", action="store_true", help="only the ns/flip grid of models and sizes")
     args = ap.parse_args()
     sw = _sw()
     sw.lib()
+    if args.matrix:
+        print(json.dumps({"ns_per_flip": timing_matrix()}))
+        return
     model = sw.SW_CLOCK if args.model == "clock" else sw.SW_POTTS
     temps = temperatures(args.q, model, args.lo, args.hi, args.n)
     rows = scan(args.q, model, args.L, temps, args.sweeps, args.equil)

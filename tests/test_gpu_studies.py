@@ -32,3 +32,13 @@ def test_binder_curves_cross_at_the_potts_critical_point(q):
     # cross once more further above T_c.)
     t = studies.crossing(rows, "U", 32, 64)
     assert t is not None and abs(t - tc) < 0.03 * tc, (t, tc)
+
+
+def test_timing_matrix_covers_the_grid():
+    """The ns/flip grid: Potts q = 2, 3, 4 at T_c for every size, clock q = 6
+    at three temperatures, each update only and with measurement."""
+    rows = studies.timing_matrix(sizes=(128, 256), sweeps=4, equil=4)
+    assert len(rows) == 3 * 2 + 3
+    assert {(r["model"], r["q"]) for r in rows} == {("potts", 2), ("potts", 3), ("potts", 4), ("clock", 6)}
+    for r in rows:
+        assert r["update_only"] > 0.0 and r["with_measurement"] > 0.0
