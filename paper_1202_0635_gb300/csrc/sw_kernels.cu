@@ -251,8 +251,10 @@ __device__ __forceinline__ uint32_t clock_classes4(uint32_t a, uint32_t b, uint3
 template <int BITS>
 struct ClassTally {
     static constexpr int kSets = (1 << BITS) - 1;
-    unsigned n = 0;           // pairs
-    unsigned m[kSets] = {};   // m[S - 1]: pairs whose class has all bits of S (S = 1 .. 2^BITS - 1)
+    unsigned n = 0;               // pairs
+    uint32_t acc[kSets] = {};     // per byte lane: pairs whose class has all bits of S (S = 1 .. 2^BITS - 1)
+    // At most 63 calls between flushes (a byte lane holds up to 255, the
+    // four lanes' sum is formed in the top byte).
     __device__ __forceinline__ void add4(uint32_t cls)
     {
         n += 4u;
@@ -262,7 +264,7 @@ struct ClassTally {
 #pragma unroll
             for (int j = 0; j < BITS; ++j)
                 if ((S >> j) & 1) b &= cls >> j;
-            m[S - 1] += __popc(b);
+            acc[S - 1] += b;
         }
     }
     // Pairs of class d: sum over S containing d of (-1)^|S - d| N_S.
@@ -272,7 +274,7 @@ struct ClassTally {
 #pragma unroll
         for (int S = 0; S <= kSets; ++S) {
             if ((S & d) != d) continue;
-            const int ns = S ? (int)m[S - 1] : (int)n;
+            const int ns = S ? (int)((acc[S - 1] * 0x01010101u) >> 24) : (int)n;
             c += (__popc(S ^ d) & 1) ? -ns : ns;
         }
         return (unsigned)c;
@@ -322,17 +324,15 @@ __device__ __forceinline__ void tally_pairs_any(unsigned int *hist, const uint32
 // k_bonds, q <= 15 (classes below 2^BITS): the nearest-neighbour pairs
 // (right, down) into hist_class, and the pairs at distance L/4 and L/2
 // (Sec. 4, G(r,T)) into hist4 and hist2.  wd, dn and sr are the row, the
-// row below and the state right of the row; wd is sanitised in place (the
-// bonds are drawn by then).  All 32 lanes of the warp.
+// row below and the state right of the row, all valid states.  All 32
+// lanes of the warp.
 template <int BITS>
 __device__ __forceinline__ void clock_row_classes(unsigned int *hist_class, unsigned int *hist4, unsigned int *hist2,
                                                   const int8_t *spin, int L, int y, int x0, int ncols, bool rv, int q,
-                                                  int nclass, uint32_t (&wd)[8], const uint32_t (&dn)[8], uint32_t sr)
+                                                  int nclass, const uint32_t (&wd)[8], const uint32_t (&dn)[8],
+                                                  uint32_t sr)
 {
     const uint32_t q4 = (uint32_t)q * 0x01010101u;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) wd[k] = clock_valid4(wd[k], q4);
-    sr = (uint32_t)valid_state((int)sr, q);
     {
         ClassTally<BITS> t;
 #pragma unroll
@@ -340,7 +340,7 @@ __device__ __forceinline__ void clock_row_classes(unsigned int *hist_class, unsi
             if (!(rv && 4 * k < ncols)) continue;   // ncols % 4 == 0
             const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
             t.add4(clock_classes4(wd[k], __funnelshift_r(wd[k], nxt, 8), q4));
-            t.add4(clock_classes4(wd[k], clock_valid4(dn[k], q4), q4));
+            t.add4(clock_classes4(wd[k], dn[k], q4));
         }
         t.flush(hist_class, nclass);
     }
@@ -362,14 +362,15 @@ __device__ __forceinline__ void clock_row_classes(unsigned int *hist_class, unsi
 // bonds and the bond classes of the incoming configuration (the previous
 // sweep's result).
 // ---------------------------------------------------------------------------
-template <bool MEASURE, bool CLOCK_MEASURE>
-__global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
+// ANY_CLOCK: the batch holds a clock lattice; the clock code is compiled in.
+// The bounds keep the clock measuring variant at 80 registers and the
+// Potts-only variants at 8 resident blocks per SM, without spills.
+template <bool MEASURE, bool ANY_CLOCK>
+__global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) : 8) k_bonds(Batch b)
 {
-    // Clock model: threshold of two projection magnitudes r_a, r_b on the
-    // same side of the sweep's mirror axis, and each state's projection
-    // (magnitude r = j mod q, side 1 or 2 in bits 6-7, 0 on the axis).
+    // Clock model: bond threshold of every state pair (a, b) for the sweep's
+    // mirror axis, zero unless both project strictly onto the same side.
     __shared__ uint32_t s_thr[SW_MAX_CLOCK_Q * SW_MAX_CLOCK_Q];
-    __shared__ uint8_t s_proj[SW_MAX_CLOCK_Q];
     __shared__ unsigned int hist_class[SW_MAX_CLOCK_Q / 2 + 2];
     __shared__ unsigned int hist_corr[2][SW_MAX_CLOCK_Q / 2 + 2];   // clock: pairs at L/4, L/2
     __shared__ unsigned int red[32];
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                 if (!lat.clock) {
                     block_add<kBlockThreads>(prev + lat.q + 1, unequal, red);
                     block_add<kBlockThreads>(prev + lat.q + 0, pairs - unequal, red);
-                } else if (CLOCK_MEASURE) {
+                } else if (ANY_CLOCK) {
                     __syncthreads();
                     const int nc = lat.nclass;
                     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
@@ -415,13 +416,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                     hist_class[k] = hist_corr[0][k] = hist_corr[1][k] = 0u;
             __syncthreads();
             if (lat.clock) {
+                // Projection of state k: j = (2k - m) mod 2q, magnitude j mod q,
+                // side 1 (j < q) or 2 (j > q), none on the axis (j = 0, q).
                 const int q = lat.q;
-                for (int i = threadIdx.x; i < q * q; i += blockDim.x)
-                    s_thr[i] = __ldg(lat.thr_tab + (i / q) * (2 * q) + (i % q));
-                for (int k = threadIdx.x; k < q; k += blockDim.x) {
-                    const int j = clock_class(k, ctx.m, q);
-                    const int side = (j == 0 || j == q) ? 0 : (j < q ? 1 : 2);
-                    s_proj[k] = (uint8_t)((j % q) | (side << 6));
+                for (int i = threadIdx.x; i < q * q; i += blockDim.x) {
+                    const int ja = clock_class(i / q, ctx.m, q), jb = clock_class(i % q, ctx.m, q);
+                    const int sa = (ja == 0 || ja == q) ? 0 : (ja < q ? 1 : 2);
+                    const int sb = (jb == 0 || jb == q) ? 0 : (jb < q ? 1 : 2);
+                    s_thr[i] = (sa != 0 && sa == sb) ? __ldg(lat.thr_tab + (ja % q) * (2 * q) + (jb % q)) : 0u;
                 }
                 __syncthreads();
             }
@@ -429,16 +431,12 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
         }
         const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
-        const bool clock = lat.clock != 0;
+        const bool clock = ANY_CLOCK && lat.clock != 0;
+        if (!ANY_CLOCK && lat.clock && threadIdx.x == 0) record_error(lat.st, kErrInternal, 0);   // wrong variant
         const unsigned long long t = ctx.t;
         const uint32_t thr = lat.thr;
-        // Clock bond threshold of states a, b (zero unless both project
-        // strictly onto the same side of the axis).
-        auto cthr = [&](int a, int c) -> uint32_t {
-            const int pa = s_proj[valid_state(a, q)], pc = s_proj[valid_state(c, q)];
-            if (((pa ^ pc) & 0xC0) || !(pa & 0xC0)) return 0u;
-            return s_thr[(pa & 63) * q + (pc & 63)];
-        };
+        // Clock bond threshold of valid states a, b.
+        auto cthr = [&](int a, int c) -> uint32_t { return s_thr[a * q + c]; };
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int X0 = bx * TW, Y0 = by * TH;
         const int tw = min(TW, L - X0), th = min(TH, L - Y0);          // valid extent of the tile
@@ -474,6 +472,15 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                 const int xr = (x0 + ncols == L) ? 0 : x0 + ncols;
                 sr = (uint8_t)__ldg(lat.spin + (size_t)y * L + xr);
             }
+        }
+        if (clock) {   // states outside [0, q) read as 0: they index the q x q threshold table
+            const uint32_t q4 = (uint32_t)q * 0x01010101u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                wd[k] = clock_valid4(wd[k], q4);
+                dn[k] = clock_valid4(dn[k], q4);
+            }
+            sr = (uint32_t)valid_state((int)sr, q);
         }
         unsigned eqR = 0, eqD = 0, rR = 0, rD = 0;
         if (!clock) {
@@ -520,8 +527,6 @@ __global__ void __launch_bounds__(kBlockThreads) k_bonds(Batch b)
                         unequal += __popc(~eqR & V) + __popc(~eqD & V);
                         pairs += 2u * (unsigned)ncols;
                     }
-                } else if (!CLOCK_MEASURE) {
-                    record_error(lat.st, kErrInternal, 0);   // a clock lattice needs the clock variant
                 } else if (lat.nclass <= 4) {
                     // q <= 7: classes in two bits, four pairs per word,
                     // tallied by bit planes and reduced over the warp.
@@ -1313,7 +1318,7 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
     };
     mark();
     const int bblocks = std::max(1, std::min(b.ntasks, sm_count * shape.bonds));
-    if (MEASURE && b.any_clock)
+    if (b.any_clock)
         k_bonds<MEASURE, true><<<bblocks, kBlockThreads, 0, s>>>(b);
     else
         k_bonds<MEASURE, false><<<bblocks, kBlockThreads, 0, s>>>(b);
@@ -1367,12 +1372,12 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
 cudaError_t launch_bonds(const Batch &b, bool measure, int sm_count, cudaStream_t s)
 {
     const int blocks = std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM));
-    if (!measure)
-        k_bonds<false, false><<<blocks, kBlockThreads, 0, s>>>(b);
-    else if (b.any_clock)
-        k_bonds<true, true><<<blocks, kBlockThreads, 0, s>>>(b);
+    if (measure)
+        b.any_clock ? k_bonds<true, true><<<blocks, kBlockThreads, 0, s>>>(b)
+                    : k_bonds<true, false><<<blocks, kBlockThreads, 0, s>>>(b);
     else
-        k_bonds<true, false><<<blocks, kBlockThreads, 0, s>>>(b);
+        b.any_clock ? k_bonds<false, true><<<blocks, kBlockThreads, 0, s>>>(b)
+                    : k_bonds<false, false><<<blocks, kBlockThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
