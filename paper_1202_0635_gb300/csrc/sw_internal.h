@@ -28,10 +28,10 @@ constexpr int kCrossWords = 4;
 // Merge items per tile: the 64 rows of its right edge, then the 64
 // columns of its bottom edge.
 constexpr int kMergeItems = 128;
-// Per-site code: closed component -> kCodeClosed | new state (below 128);
-// open component -> slot of its root in the tile's open list (below 256).
-// A Potts code thus indexes one table: the open slots' new states, then
-// entry kCodeClosed + s = s.
+// Per-site code: closed component -> kCodeClosed | new state (Potts, below
+// 128) or kCodeClosed | reflection flag (clock); open component -> slot of
+// its root in the tile's open list (below 256).  A Potts code thus indexes
+// one table: the open slots' new states, then entry kCodeClosed + s = s.
 constexpr uint16_t kCodeClosed = 0x100;
 
 // Bond-mask words per tile (right and down bonds of 64 rows, 2 words a row).

@@ -115,11 +115,12 @@ __device__ __forceinline__ void queue_union(uint32_t *pairs, int idx, int a, int
     else if (!union_t(par, a, b, kTileSites + 1)) record_error(st, kErrUnionCap, where);
 }
 
-// Per-site code of a resolved word (clock closed clusters: refined per site).
+// Per-site code of a resolved word: closed -> kCodeClosed | new state
+// (Potts) or | reflection flag (clock); open -> slot.
 __device__ __forceinline__ uint32_t code_of(int w)
 {
     if (w < 0) return kCodeClosed;
-    return (w & kResClosed) ? (kCodeClosed | (uint32_t)(w & 0x7F)) : (uint32_t)(w & 0xFF);
+    return (w & kResClosed) ? (kCodeClosed | (uint32_t)(w & 0x7F) | ((w & kResFlip) ? 1u : 0u)) : (uint32_t)(w & 0xFF);
 }
 
 __device__ __forceinline__ int reflect(int k, int m, int q)
@@ -612,7 +613,6 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         const int L = lat.L, q = lat.q;
         const bool clock = lat.clock != 0;
         const unsigned long long t = ctx.t;
-        const int m = ctx.m;
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int X0 = bx * TW, Y0 = by * TH;
         const int tw = min(TW, L - X0), th = min(TH, L - Y0);          // valid extent of the tile
@@ -919,18 +919,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                     w0 = w1 = -1;
                 }
                 const size_t site = (size_t)(Y0 + row) * L + X0 + c0;
-                uint32_t code0 = code_of(w0), code1 = code_of(w1);
-                if (clock && ((code0 | code1) & kCodeClosed)) {
-                    const char2 k2 = *reinterpret_cast<const char2 *>(lat.spin + site);
-                    if (code0 & kCodeClosed) {
-                        const int k0 = valid_state(k2.x, q);
-                        code0 = kCodeClosed | (uint32_t)((w0 & kResFlip) ? reflect(k0, m, q) : k0);
-                    }
-                    if (code1 & kCodeClosed) {
-                        const int k1 = valid_state(k2.y, q);
-                        code1 = kCodeClosed | (uint32_t)((w1 & kResFlip) ? reflect(k1, m, q) : k1);
-                    }
-                }
+                const uint32_t code0 = code_of(w0), code1 = code_of(w1);
                 if (LABELS) {
                     if (code0 & kCodeClosed) lat.label[site] = tile_site(L, bx, by, x0n);
                     if (code1 & kCodeClosed) lat.label[site + 1] = tile_site(L, bx, by, x1n);
@@ -1176,9 +1165,9 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? 8 : 10) k_flip_tile
             for (int h = 0; h < 4; ++h) {
                 const uint32_t code = ((h < 2) ? (cw[k].x >> (16 * h)) : (cw[k].y >> (16 * (h - 2)))) & 0xFFFFu;
                 int ns;
-                if (clock) {
+                if (clock) {   // closed: the cluster's flag in the code; open: its root's, in the table
                     const int k0 = valid_state((int)((sw[k] >> (8 * h)) & 0xFFu), q);
-                    ns = (code & kCodeClosed) ? (int)(code & 0x7Fu) : (tab[code & 0xFFu] ? reflect(k0, m, q) : k0);
+                    ns = ((code & kCodeClosed) ? (code & 1u) : tab[code & 0xFFu]) ? reflect(k0, m, q) : k0;
                 } else {
                     ns = tab[min(code, (uint32_t)(kOpenSlots + SW_MAX_Q - 1))];   // open slot or kCodeClosed | state
                 }
