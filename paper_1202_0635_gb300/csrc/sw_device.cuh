@@ -42,7 +42,7 @@ struct Lattice {
     uint16_t *code;             // L*L per-site codes written by the labeling stage
     int32_t *open_list;         // tiles x kOpenSlots global indices of open tile roots
     int32_t *open_count;        // tiles
-    uint32_t *cross;            // tiles x 2 words: active crossing bonds (right edge rows, bottom edge columns)
+    uint32_t *cross;            // tiles x kCrossWords: active crossing bonds (right edge rows, bottom edge columns)
     uint32_t *bond;             // tiles x 256 words: a tile's right-bond masks (64 rows x 2 words), then
                                 // its down-bond masks; bit c of word (row, h) = bond of column 32 h + c
     int tiles_x, tiles_y;
