@@ -63,6 +63,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def max_sm_mhz():
+    """Maximum SM clock: MEASURED_PEAKS.json, else the GB300's 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples (every 100 ms) while the
     sweeps run.  Started before the warm-up and waited for, so that it is
@@ -377,13 +386,15 @@ def run_ours(args, world, rank, local):
     dom_name = STAGES[dom]
     dom_bytes = ALG_BYTES_PER_SITE[dom_name]
     achieved = (dom_bytes * N) / (prof[dom] * 1e-3) / 1e9 if dom_bytes else None
-    traffic = None
+    traffic, winst = None, None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
-            traffic = json.load(open(tfile)).get(dom_name)
+            tj = json.load(open(tfile))
+            traffic = tj.get(dom_name)
+            winst = tj.get("warp_instructions", {}).get(dom_name)
         except Exception:
-            traffic = None
+            traffic, winst = None, None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": peak_kind, "bytes_per_site": dom_bytes}
@@ -391,6 +402,14 @@ def run_ours(args, world, rank, local):
                       "achieved": SWEEP_BYTES_PER_SITE * N / (ms_per_step * 1e-3) / 1e9,
                       "peak": peak, "unit": "GB/s"}
     sweep_roofline["frac"] = sweep_roofline["achieved"] / peak
+    # The dominant kernel is bound by instruction issue, not by DRAM: its
+    # warp instructions per launch (ncu, same capture as the traffic) over
+    # its event time, against one issue per SM sub-partition per cycle.
+    issue_peak = torch.cuda.get_device_properties(0).multi_processor_count * 4 * max_sm_mhz() * 1e-3   # G/s
+    issue_roofline = {"kernel": dom_name, "unit": "G warp instructions/s", "peak": issue_peak,
+                      "warp_instructions": winst,
+                      "achieved": (winst / (prof[dom] * 1e-3) / 1e9) if winst else None}
+    issue_roofline["frac"] = (issue_roofline["achieved"] / issue_peak) if winst else None
 
     # ---- update-only timing (the paper's other row), same procedure
     sw.sw_set_measure(lat.h, 0)
@@ -464,6 +483,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single lattice"},
         "roofline": roofline,
         "sweep_roofline": sweep_roofline,
+        "issue_roofline": issue_roofline,
         "stage_us": stage_us,
         "update_only_ns_per_flip": update_only,
         "batched": batched,
