@@ -180,6 +180,7 @@ struct sw_batch {
     int ntasks = 0;
     long long nmerge = 0;
     bool any_clock = false;
+    int nrep = 0;                 // lattices in the descriptor arrays
     bool dirty = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -191,7 +192,7 @@ struct sw_batch {
         b.task_off = d_task_off;
         b.merge_off = d_merge_off;
         b.ticket = d_ticket;
-        b.nrep = (int)reps.size();
+        b.nrep = nrep;
         b.ntasks = ntasks;
         b.nmerge = nmerge;
         b.any_clock = any_clock;
@@ -1032,10 +1033,13 @@ static int rebuild_batch(sw_batch *b)
     }
     bool any_clock = false;
     for (int i = 0; i < n; ++i) any_clock = any_clock || b->reps[i]->model == SW_CLOCK;
-    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge || any_clock != b->any_clock) drop_batch_graph(b);
+    // A captured graph holds the kernel parameters of the batch view.
+    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge || any_clock != b->any_clock || n != b->nrep)
+        drop_batch_graph(b);
     b->ntasks = task_off[n];
     b->nmerge = merge_off[n];
     b->any_clock = any_clock;
+    b->nrep = n;
     if (n) {
         SW_CUDA(cudaMemcpyAsync(b->d_lat, lat.data(), sizeof(Lattice) * n, cudaMemcpyHostToDevice, b->stream));
         SW_CUDA(cudaMemcpyAsync(b->d_task_off, task_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,

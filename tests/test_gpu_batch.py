@@ -87,6 +87,27 @@ def test_attach_detach_mid_run_keeps_each_chain():
     b.close()
 
 
+def test_graph_rebuilt_when_the_lattice_count_changes():
+    """Four 64^2 lattices and one 128^2 lattice have the same tile and merge
+    item counts; swapping one set for the other under a captured graph must
+    still sweep the new set correctly."""
+    Tc = 1.0 / math.log(1.0 + math.sqrt(2.0))
+    b = sw.Batch()
+    sw.sw_batch_set_graph(b.b, 1)
+    small = [b.add(64, 2, sw.SW_POTTS, Tc, 10 + i, init=sw.SW_INIT_RANDOM) for i in range(4)]
+    b.sweep(3)
+    for lat in small:
+        b.remove(lat)
+        lat.close()
+    big = b.add(128, 2, sw.SW_POTTS, Tc, 20, init=sw.SW_INIT_RANDOM)
+    b.sweep(3)
+    o = Oracle(128, 2, POTTS, Tc, 20, init="random")
+    o.sweep(3)
+    assert np.array_equal(big.spins, o.spins)
+    o.close()
+    b.close()
+
+
 def test_batch_measure_off_and_labels():
     Tc = 1.0 / math.log(1.0 + math.sqrt(3.0))
     b = sw.Batch()
