@@ -1283,17 +1283,69 @@ __global__ void __launch_bounds__(kEnergyThreads) k_pending_classes(Lattice lat)
     }
 }
 
+// The same for the Potts model when rows are 16-byte aligned: sixteen sites
+// per thread from one 16-byte load of the row and one of the row below.
+__device__ __forceinline__ unsigned int zero_byte_count(uint32_t x)
+{
+    return __popc(~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu));
+}
+
+__global__ void __launch_bounds__(kEnergyThreads) k_pending_unequal(Lattice lat)
+{
+    __shared__ unsigned int red[32];
+    const unsigned long long t = read_u64(&lat.st->sweep);
+    if (t == 0ull || t - 1ull < read_u64(&lat.st->classes_upto)) return;   // same for every block
+    const int L = lat.L, per_row = L / 16;
+    const int n16 = L * per_row;   // L * L < 2^31
+    unsigned int unequal = 0, pairs = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n16; g += gridDim.x * blockDim.x) {
+        const int y = g / per_row, xq = g - y * per_row;
+        const int yd = y + 1 == L ? 0 : y + 1;
+        const uint4 a = reinterpret_cast<const uint4 *>(lat.spin + (size_t)y * L)[xq];
+        const uint4 d = reinterpret_cast<const uint4 *>(lat.spin + (size_t)yd * L)[xq];
+        const uint32_t r = (uint8_t)lat.spin[(size_t)y * L + (16 * xq + 16 == L ? 0 : 16 * xq + 16)];
+        const uint32_t w[5] = {a.x, a.y, a.z, a.w, r};
+        const uint32_t dn[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            unequal += 8u - zero_byte_count(w[k] ^ __funnelshift_r(w[k], w[k + 1], 8)) - zero_byte_count(w[k] ^ dn[k]);
+        pairs += 32u;
+    }
+    unsigned long long *row = ring_row(lat, t - 1);
+    block_add<kEnergyThreads>(row + lat.q + 1, unequal, red);
+    block_add<kEnergyThreads>(row + lat.q + 0, pairs - unequal, red);
+}
+
 __global__ void k_mark_classes(DevState *st)
 {
     st->classes_upto = st->sweep;
 }
 
-// Count states outside [0, q) (spins written by the caller).
+// States outside [0, q) (q <= 127) in the spin array: sixteen per 16-byte
+// load where the array is aligned (a byte is out of range if its top bit
+// is set or its low seven bits reach q), one at a time otherwise.
+__device__ __forceinline__ unsigned int out_of_range4(uint32_t x, uint32_t q4)
+{
+    return __popc((((x & 0x7F7F7F7Fu) + (0x80808080u - q4)) | x) & 0x80808080u);
+}
+
 __global__ void k_count_invalid(const int8_t *spin, long long n, int q, unsigned int *bad)
 {
     unsigned int c = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        c += (spin[i] < 0 || spin[i] >= q);
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long done = 0;
+    if ((reinterpret_cast<uintptr_t>(spin) & 15) == 0) {
+        const uint32_t q4 = (uint32_t)q * 0x01010101u;
+        const uint4 *v = reinterpret_cast<const uint4 *>(spin);
+        const long long n16 = n / 16;
+        for (long long i = tid; i < n16; i += stride) {
+            const uint4 w = v[i];
+            c += out_of_range4(w.x, q4) + out_of_range4(w.y, q4) + out_of_range4(w.z, q4) + out_of_range4(w.w, q4);
+        }
+        done = n16 * 16;
+    }
+    for (long long i = done + tid; i < n; i += stride) c += (spin[i] < 0 || spin[i] >= q);
     c = __reduce_add_sync(FULL, c);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
 }
@@ -1344,6 +1396,8 @@ cudaError_t launch_pending_classes(const Lattice &lat, int sm_count, cudaStream_
         (int)std::min<long long>((N4 + kEnergyThreads - 1) / kEnergyThreads, (long long)sm_count * 8);
     if (lat.clock)
         k_pending_classes<true><<<blocks, kEnergyThreads, 0, s>>>(lat);
+    else if (lat.L % 16 == 0 && (reinterpret_cast<uintptr_t>(lat.spin) & 15) == 0)
+        k_pending_unequal<<<blocks, kEnergyThreads, 0, s>>>(lat);
     else
         k_pending_classes<false><<<blocks, kEnergyThreads, 0, s>>>(lat);
     k_mark_classes<<<1, 1, 0, s>>>(lat.st);
@@ -1353,7 +1407,7 @@ cudaError_t launch_pending_classes(const Lattice &lat, int sm_count, cudaStream_
 cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_count, cudaStream_t s)
 {
     const long long n = (long long)lat.L * lat.L;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)sm_count * 4);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
     k_count_invalid<<<blocks, 256, 0, s>>>(lat.spin, n, lat.q, bad);
     return cudaGetLastError();
 }
