@@ -96,6 +96,11 @@ struct sw_handle {
     int labeling = SW_LABEL_TILED;
     int32_t *d_R = nullptr;
     unsigned int *d_flag = nullptr, *h_flag = nullptr;
+    // Pinned staging of a counter drain (rows, device state block), so that
+    // its copies are asynchronous and one stream synchronisation suffices.
+    unsigned long long *h_rows = nullptr;
+    size_t h_rows_cap = 0;
+    DevState *h_st = nullptr;
     int last_passes = 0;
     uint32_t thr = 0;
     std::vector<uint32_t> thr_tab;
@@ -281,11 +286,9 @@ void accumulate(sw_handle *h, const int64_t *row)
     if (h->record) h->history.insert(h->history.end(), row, row + h->ncounters);
 }
 
-int check_device_error(sw_handle *h)
+// Fold the device state block's error word into the handle's sticky status.
+int sticky_from(sw_handle *h, const DevState &st)
 {
-    DevState st;
-    SW_CUDA(cudaMemcpyAsync(&st, h->d_st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
-    SW_CUDA(cudaStreamSynchronize(h->stream));
     if (st.err != swgb::kErrNone && h->sticky == SW_OK) {
         h->sticky = SW_ERR_NOT_CONVERGED;
         char buf[160];
@@ -296,36 +299,56 @@ int check_device_error(sw_handle *h)
     return SW_OK;
 }
 
+int check_device_error(sw_handle *h)
+{
+    DevState st;
+    SW_CUDA(cudaMemcpyAsync(&st, h->d_st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    return sticky_from(h, st);
+}
+
 // Wait for the stream and fold every pending measured sweep into the host
 // statistics, oldest first.
 int drain(sw_handle *h)
 {
-    SW_CUDA(cudaStreamSynchronize(h->stream));
     const uint64_t pending = h->t_host - h->t_drained;
-    if (pending > 0 && h->measure) {
+    const bool rows = pending > 0 && h->measure;
+    const size_t nc = (size_t)h->ncounters;
+    if (!h->h_st) SW_CUDA(cudaHostAlloc(&h->h_st, sizeof(DevState), cudaHostAllocDefault));
+    if (rows && h->h_rows_cap < (size_t)pending * nc) {
+        if (h->h_rows) cudaFreeHost(h->h_rows);
+        h->h_rows = nullptr;
+        h->h_rows_cap = 0;
+        const size_t cap = std::max((size_t)pending, (size_t)8) * nc;
+        SW_CUDA(cudaHostAlloc(&h->h_rows, cap * sizeof(unsigned long long), cudaHostAllocDefault));
+        h->h_rows_cap = cap;
+    }
+    if (rows) {
         // The bond classes of the newest configuration are normally counted
         // by the next sweep's labeling pass; count them now.
         cudaError_t e = swgb::launch_pending_classes(h->lattice(), h->sm_count, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launch_pending_classes");
         // Copy only the pending rows (at most two contiguous ring segments).
-        const size_t nc = (size_t)h->ncounters;
-        std::vector<unsigned long long> rows((size_t)pending * nc);
         const size_t first = (size_t)(h->t_drained % swgb::kRingSlots);
         const size_t n1 = std::min((size_t)pending, (size_t)swgb::kRingSlots - first);
-        SW_CUDA(cudaMemcpyAsync(rows.data(), h->d_ring + first * nc, n1 * nc * sizeof(unsigned long long),
+        SW_CUDA(cudaMemcpyAsync(h->h_rows, h->d_ring + first * nc, n1 * nc * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, h->stream));
         if (n1 < pending)
-            SW_CUDA(cudaMemcpyAsync(rows.data() + n1 * nc, h->d_ring, ((size_t)pending - n1) * nc *
+            SW_CUDA(cudaMemcpyAsync(h->h_rows + n1 * nc, h->d_ring, ((size_t)pending - n1) * nc *
                                     sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
-        SW_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    // The device state block (error word), behind everything enqueued so far.
+    SW_CUDA(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    if (rows) {
         std::vector<int64_t> row(nc);
         for (size_t k = 0; k < (size_t)pending; ++k) {
-            for (size_t c = 0; c < nc; ++c) row[c] = (int64_t)rows[k * nc + c];
+            for (size_t c = 0; c < nc; ++c) row[c] = (int64_t)h->h_rows[k * nc + c];
             accumulate(h, row.data());
         }
     }
     h->t_drained = h->t_host;
-    return check_device_error(h);
+    return sticky_from(h, *h->h_st);
 }
 
 int reset_device_index(sw_handle *h, uint64_t t)
@@ -483,6 +506,8 @@ void free_handle(sw_handle *h)
     if (h->d_R) cudaFree(h->d_R);
     if (h->d_flag) cudaFree(h->d_flag);
     if (h->h_flag) cudaFreeHost(h->h_flag);
+    if (h->h_rows) cudaFreeHost(h->h_rows);
+    if (h->h_st) cudaFreeHost(h->h_st);
     if (h->d_bond) cudaFree(h->d_bond);
     if (h->d_st) cudaFree(h->d_st);
     if (h->d_ring) cudaFree(h->d_ring);
