@@ -44,10 +44,12 @@ constexpr int kInfLabel = 1 << 20;      // "no label" (larger than any tile node
 constexpr int kMaxPairs = 1024;         // queued unions per tile (more are joined at once)
 constexpr int kWarpPairs = kMaxPairs / kTaskWarps;   // each warp queues into its own segment
 constexpr int kFreshList = 2 * kMaxPairs;  // fresh labels listed per tile (more: settled in place)
-// Resolved root word: kTileResolved | kResClosed | state (or kResFlip), or
-// kTileResolved | open slot.
-constexpr int kResClosed = 0x800, kResFlip = 0x400;
-static_assert(SW_MAX_Q <= 0x80 && kOpenSlots <= 0x100, "resolved words hold a state or a slot");
+// Resolved root word: kTileResolved | the cluster's per-site code, i.e.
+// kCodeClosed | new state (Potts) or reflection flag (clock), or the open
+// slot.
+constexpr int kCodeMask = 0x1FF;
+static_assert(SW_MAX_Q <= 0x80 && kOpenSlots <= 0x100 && kCodeClosed == 0x100 && kTileResolved > kCodeMask,
+              "resolved words hold a code");
 
 static_assert(QW == 32, "a warp quadrant is 32 x 32: lane r owns row r as a 32-bit mask");
 static_assert(TW == 2 * QW && TH == 2 * QW, "a tile is 2 x 2 quadrants");
@@ -115,13 +117,6 @@ __device__ __forceinline__ void queue_union(uint32_t *pairs, int idx, int a, int
     else if (!union_t(par, a, b, kTileSites + 1)) record_error(st, kErrUnionCap, where);
 }
 
-// Per-site code of a resolved word: closed -> kCodeClosed | new state
-// (Potts) or | reflection flag (clock); open -> slot.
-__device__ __forceinline__ uint32_t code_of(int w)
-{
-    if (w < 0) return kCodeClosed;
-    return (w & kResClosed) ? (kCodeClosed | (uint32_t)(w & 0x7F) | ((w & kResFlip) ? 1u : 0u)) : (uint32_t)(w & 0xFF);
-}
 
 __device__ __forceinline__ int reflect(int k, int m, int q)
 {
@@ -858,11 +853,11 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                     w = kTileResolved | slot;
                 } else {
                     record_error(lat.st, kErrInternal, g);
-                    w = kTileResolved | kResClosed;
+                    w = kTileResolved | kCodeClosed;
                 }
             } else {
                 const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
-                w = kTileResolved | kResClosed | (clock ? ((u >> 31) ? kResFlip : 0) : mulhi_q(u, q));
+                w = kTileResolved | kCodeClosed | (clock ? (int)(u >> 31) : mulhi_q(u, q));
                 ++closed_roots;
             }
             par[tile_slot(v)] = (uint16_t)w;
@@ -916,10 +911,10 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                 }
                 if (w0 < kTileResolved || w1 < kTileResolved) {   // unreachable for a settled tile
                     record_error(lat.st, kErrInternal, Y0 * L + X0);
-                    w0 = w1 = -1;
+                    w0 = w1 = kTileResolved | kCodeClosed;
                 }
                 const size_t site = (size_t)(Y0 + row) * L + X0 + c0;
-                const uint32_t code0 = code_of(w0), code1 = code_of(w1);
+                const uint32_t code0 = (uint32_t)(w0 & kCodeMask), code1 = (uint32_t)(w1 & kCodeMask);
                 if (LABELS) {
                     if (code0 & kCodeClosed) lat.label[site] = tile_site(L, bx, by, x0n);
                     if (code1 & kCodeClosed) lat.label[site + 1] = tile_site(L, bx, by, x1n);
