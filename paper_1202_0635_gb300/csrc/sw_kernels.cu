@@ -892,34 +892,36 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         }
         __syncthreads();
 
-        // ===== codes: lane = column pair, one row per warp step ================
-        const int c0 = 2 * lane;
-        if (c0 < tw) {   // tw % 4 == 0: both columns or neither
-            for (int row = warp; row < th; row += kTaskWarps) {
-                const uint32_t lp = reinterpret_cast<const uint32_t *>(lbl)[(row * TW + c0) >> 1];
-                int x0n = (int)(lp & 0xFFFFu), x1n = (int)(lp >> 16);
-                int w0 = par_ld(par, x0n), w1 = par_ld(par, x1n);
+        // ===== codes: lane = four columns, two rows per warp step ==============
+        const int c4 = 4 * (lane & 15);
+        if (c4 < tw) {   // tw % 4 == 0: all four columns or none
+            for (int row = 2 * warp + (lane >> 4); row < th; row += 2 * kTaskWarps) {
+                const uint2 lp = reinterpret_cast<const uint2 *>(lbl)[(row * TW + c4) >> 2];
+                int xn[4] = {(int)(lp.x & 0xFFFFu), (int)(lp.x >> 16), (int)(lp.y & 0xFFFFu), (int)(lp.y >> 16)};
+                int w[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) w[k] = par_ld(par, xn[k]);
                 if (LABELS) {   // a label's word is resolved (a root) or names its root
-                    if (w0 < kTileResolved) {
-                        x0n = w0;
-                        w0 = par_ld(par, w0);
-                    }
-                    if (w1 < kTileResolved) {
-                        x1n = w1;
-                        w1 = par_ld(par, w1);
-                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (w[k] < kTileResolved) {
+                            xn[k] = w[k];
+                            w[k] = par_ld(par, w[k]);
+                        }
                 }
-                if (w0 < kTileResolved || w1 < kTileResolved) {   // unreachable for a settled tile
+                if (!(w[0] & w[1] & w[2] & w[3] & kTileResolved)) {   // unreachable for a settled tile
                     record_error(lat.st, kErrInternal, Y0 * L + X0);
-                    w0 = w1 = kTileResolved | kCodeClosed;
+                    w[0] = w[1] = w[2] = w[3] = kTileResolved | kCodeClosed;
                 }
-                const size_t site = (size_t)(Y0 + row) * L + X0 + c0;
-                const uint32_t code0 = (uint32_t)(w0 & kCodeMask), code1 = (uint32_t)(w1 & kCodeMask);
+                const size_t site = (size_t)(Y0 + row) * L + X0 + c4;
+                const uint2 codes = make_uint2(((uint32_t)w[0] | ((uint32_t)w[1] << 16)) & (kCodeMask * 0x10001u),
+                                               ((uint32_t)w[2] | ((uint32_t)w[3] << 16)) & (kCodeMask * 0x10001u));
                 if (LABELS) {
-                    if (code0 & kCodeClosed) lat.label[site] = tile_site(L, bx, by, x0n);
-                    if (code1 & kCodeClosed) lat.label[site + 1] = tile_site(L, bx, by, x1n);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (w[k] & kCodeClosed) lat.label[site + k] = tile_site(L, bx, by, xn[k]);
                 }
-                *reinterpret_cast<uint32_t *>(lat.code + site) = code0 | (code1 << 16);
+                *reinterpret_cast<uint2 *>(lat.code + site) = codes;
             }
         }
         if (threadIdx.x == 0) lat.open_count[tile] = min(s_nopen, kOpenSlots);
