@@ -41,8 +41,10 @@ constexpr int kBlockThreads = kTaskWarps * 32;
 constexpr int kEnergyThreads = 256;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kInfLabel = 1 << 20;      // "no label" (larger than any tile node)
-constexpr int kMaxPairs = 1024;         // queued unions per tile (more are joined at once)
-constexpr int kWarpPairs = kMaxPairs / kTaskWarps;   // each warp queues into its own segment
+// Queued unions per tile (a row of a quadrant makes at most 31 requests;
+// random bonds make about 260 a tile at T_c).  A tile whose requests exceed
+// the queue joins all its internal bonds after the scan instead.
+constexpr int kMaxPairs = 2048;
 constexpr int kFreshList = 2 * kMaxPairs;  // fresh labels listed per tile (more: settled in place)
 // Resolved root word: kTileResolved | the cluster's per-site code, i.e.
 // kCodeClosed | new state (Potts) or reflection flag (clock), or the open
@@ -55,7 +57,6 @@ static_assert(QW == 32, "a warp quadrant is 32 x 32: lane r owns row r as a 32-b
 static_assert(TW == 2 * QW && TH == 2 * QW, "a tile is 2 x 2 quadrants");
 static_assert(sizeof(Lattice) % 8 == 0, "lattice descriptors are copied in 8-byte words");
 static_assert(TW == 64 && kBlockThreads == NS / 32, "lane = column pair; thread t owns labels 32 t .. 32 t + 31");
-static_assert(kTaskWarps == 4, "one union queue per quadrant warp, four segments");
 
 __device__ __forceinline__ unsigned long long read_u64(const unsigned long long *p)
 {
@@ -110,12 +111,6 @@ __device__ __forceinline__ int byte_at(const uint32_t (&w)[8], int c)
 
 // Union of labels a and b, queued in slot idx of the tile's list, or done at
 // once when the list is full.
-__device__ __forceinline__ void queue_union(uint32_t *pairs, int idx, int a, int b, volatile uint16_t *par,
-                                            DevState *st, int where)
-{
-    if (idx < kWarpPairs) pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
-    else if (!union_t(par, a, b, kTileSites + 1)) record_error(st, kErrUnionCap, where);
-}
 
 
 __device__ __forceinline__ int reflect(int k, int m, int q)
@@ -557,6 +552,25 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
     flush();
 }
 
+// Every bond inside a tile joined in the shared union-find: the fallback of
+// a tile whose union requests overflow the queue.  rowR / rowD hold the
+// tile-internal right and down bonds of each row (two 32-bit halves).
+__device__ __noinline__ void join_tile_bonds(volatile uint16_t *par, const uint16_t *lbl,
+                                             const unsigned int (*rowR)[2], const unsigned int (*rowD)[2], int tw,
+                                             int th, DevState *st, int where)
+{
+    for (int item = threadIdx.x; item < 2 * kTileSites; item += blockDim.x) {
+        const int node = item >> 1, down = item & 1;
+        const int r = node / kTileW, c = node % kTileW;
+        if (r >= th || c >= tw) continue;
+        const unsigned bits = down ? rowD[r][c >> 5] : rowR[r][c >> 5];
+        if (!((bits >> (c & 31)) & 1u)) continue;
+        const int other = down ? node + kTileW : node + 1;
+        if (!union_t(par, lbl[node], lbl[other], kTileSites + 1)) record_error(st, kErrUnionCap, where);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // k_label_tiles
 //
@@ -575,7 +589,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
     __shared__ __align__(8) unsigned int rowR[TH][2], rowD[TH][2];
     __shared__ unsigned int openw[NS / 32];
     __shared__ int rmin_all[kTaskWarps][QW];                // per-warp run minima of the scan
-    __shared__ int s_nopen, s_npairs[kTaskWarps], s_wsum[kTaskWarps];
+    __shared__ int s_nopen, s_npairs, s_wsum[kTaskWarps];
     __shared__ unsigned int s_cross[kCrossWords];
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
@@ -622,7 +636,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
 
         for (int i = threadIdx.x; i < NS / 32; i += blockDim.x) openw[i] = 0u;
         if (threadIdx.x == 0) s_nopen = 0;
-        if (threadIdx.x < kTaskWarps) s_npairs[threadIdx.x] = 0;
+        if (threadIdx.x == 0) s_npairs = 0;
 
         // ===== bond masks of my quadrant (written by k_bonds), lane = row ======
         if (qa) {
@@ -666,11 +680,8 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
             const bool cv = c < ncols;
             const unsigned bit = 1u << c;
             const unsigned upto = FULL >> (31 - c);   // columns <= c
-            const unsigned lanes_lt = bit - 1u;
             const int nb = (QW * qy) * TW + QW * qx;  // node of the quadrant's corner
             int *rmin = rmin_all[warp];
-            uint32_t *wq = upairs + warp * kWarpPairs;   // this warp's union queue
-            int nq = 0;                               // pairs queued so far (warp-uniform)
             int pl = 0;                               // label of the site above (valid where Dp has my bit)
             uint32_t lastq = 0xFFFFFFFFu;             // pair this lane queued last
             unsigned Dp = 0u, Rp = 0u;
@@ -698,46 +709,30 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
                 const unsigned E = Dp & ~((Dp & Rp & Rr) << 1);
                 const uint32_t pair = (uint32_t)pl | ((uint32_t)mlab << 16);
                 const bool u = (E & bit) && pl != mlab && pair != lastq;
-                const unsigned bu = __ballot_sync(FULL, u);
-                if (bu) {
-                    if (nq + __popc(bu) > kWarpPairs) __syncwarp();   // full: joined at once, after this row's stores
-                    if (u) {
-                        queue_union(wq, nq + __popc(bu & lanes_lt), pl, mlab, par, lat.st, Y0 * L + X0);
-                        lastq = pair;
-                    }
-                    nq += __popc(bu);
+                if (u) {   // a slot of its own: no warp vote on the row's path
+                    const int idx = atomicAdd(&s_npairs, 1);
+                    if (idx < kMaxPairs) upairs[idx] = pair;
+                    lastq = pair;
                 }
                 __syncwarp();
                 pl = mlab;
                 Rp = Rr;
                 Dp = __shfl_sync(FULL, Dq, row);
             }
-            if (lane == 0) s_npairs[warp] = min(nq, kWarpPairs);
         }
         __syncthreads();
 
+        // A queue overflow (block-uniform): join every bond inside the tile.
+        if (s_npairs > kMaxPairs) join_tile_bonds(par, lbl, rowR, rowD, tw, th, lat.st, Y0 * L + X0);
+
         // ===== unions: queued pairs, then the seams between the quadrants =====
         {
-            const int n0 = s_npairs[0], n1 = s_npairs[1], n2 = s_npairs[2], n3 = s_npairs[3];
-            const int np = n0 + n1 + n2 + n3;
+            const int np = min(s_npairs, kMaxPairs);
             const int nitems = np + TH + TW;
             for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
                 int a, c;
-                if (i < np) {   // item i -> segment w, entry k
-                    int k = i, w = 0;
-                    if (k >= n0) {
-                        k -= n0;
-                        w = 1;
-                        if (k >= n1) {
-                            k -= n1;
-                            w = 2;
-                            if (k >= n2) {
-                                k -= n2;
-                                w = 3;
-                            }
-                        }
-                    }
-                    const uint32_t pr = upairs[w * kWarpPairs + k];
+                if (i < np) {
+                    const uint32_t pr = upairs[i];
                     a = (int)(pr & 0xFFFFu);
                     c = (int)(pr >> 16);
                 } else if (i < np + TH) {   // column 31 - 32 of row y
