@@ -46,6 +46,9 @@ constexpr int kInfLabel = 1 << 20;      // "no label" (larger than any tile node
 // the queue joins all its internal bonds after the scan instead.
 constexpr int kMaxPairs = 2048;
 constexpr int kFreshList = 2 * kMaxPairs;  // fresh labels listed per tile (more: settled in place)
+// Resident blocks per SM of the flip kernel's variants (its launch bounds);
+// its grid never asks for more, so that one wave covers the tiles.
+constexpr int kFlipResidentPotts = 10, kFlipResidentClock = 8;
 // Resolved root word: kTileResolved | the cluster's per-site code, i.e.
 // kCodeClosed | new state (Potts) or reflection flag (clock), or the open
 // slot.
@@ -1044,7 +1047,7 @@ __device__ void finish_sweep(const Batch &b)
 // per quadrant.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS, bool ANY_CLOCK>
-__global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? 8 : 10) k_flip_tiles(Batch b)   // Potts: 10 blocks / SM
+__global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock : kFlipResidentPotts) k_flip_tiles(Batch b)
 {
     // New state (Potts) or reflection flag (clock) of each open slot; then
     // entry kCodeClosed + s = s, so that a Potts code indexes its new state.
@@ -1362,7 +1365,8 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
         (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * shape.merge));
     k_merge<<<mblocks, 256, 0, s>>>(b);
     mark();
-    const int fblocks = std::max(1, std::min(b.ntasks, sm_count * shape.flip));
+    const int fblocks = std::max(
+        1, std::min(b.ntasks, sm_count * std::min(shape.flip, b.any_clock ? kFlipResidentClock : kFlipResidentPotts)));
     if (b.any_clock)
         k_flip_tiles<MEASURE, LABELS, true><<<fblocks, kBlockThreads, 0, s>>>(b);
     else
