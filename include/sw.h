@@ -180,7 +180,9 @@ int sw_get_sweep(sw_handle *h, uint64_t *out);
 int sw_set_sweep(sw_handle *h, uint64_t t);
 
 /* Launch shape: resident blocks per SM requested for the four kernels of
- * a sweep, shape[4] = {labeling, merge, flip, bonds}, each in [1, 64].
+ * a sweep, shape[4] = {labeling, merge, flip, bonds}, each in [1, 64]
+ * (default {8, 16, 10, 16}; the flip grid never exceeds the blocks its
+ * kernel keeps resident, 10 per SM, 8 with a clock lattice).
  * Results never depend on it.  sw_autotune times every candidate (n real
  * sweeps each, they advance the chain like any others), keeps the fastest
  * per kernel, caches it per (device, work size) for the process, and writes
