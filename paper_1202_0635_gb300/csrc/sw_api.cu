@@ -79,7 +79,9 @@ struct sw_handle {
     int32_t *d_label = nullptr;
     uint32_t *d_thr_tab = nullptr;
     uint16_t *d_code = nullptr;
-    int32_t *d_open_list = nullptr, *d_open_count = nullptr;
+    unsigned long long *d_opar = nullptr;
+    uint8_t *d_edge = nullptr;
+    int32_t *d_open_count = nullptr;
     uint32_t *d_cross = nullptr;
     uint32_t *d_bond = nullptr;
     int tiles_x = 0, tiles_y = 0;
@@ -134,7 +136,8 @@ struct sw_handle {
         lat.spin = d_spin;
         lat.label = d_label;
         lat.code = d_code;
-        lat.open_list = d_open_list;
+        lat.opar = d_opar;
+        lat.edge = d_edge;
         lat.open_count = d_open_count;
         lat.cross = d_cross;
         lat.bond = d_bond;
@@ -364,6 +367,26 @@ int reset_device_index(sw_handle *h, uint64_t t)
     return SW_OK;
 }
 
+// The label array of h, allocated (and zeroed) on first use; the device
+// descriptors that hold its address are rewritten.
+int ensure_labels(sw_handle *h)
+{
+    if (h->d_label) return SW_OK;
+    const size_t n = (size_t)h->L * h->L * sizeof(int32_t);
+    cudaError_t e = cudaMalloc(&h->d_label, n);
+    if (e != cudaSuccess) {
+        h->d_label = nullptr;
+        return fail(SW_ERR_OOM, "cudaMalloc(labels, %zu bytes): %s", n, cudaGetErrorString(e));
+    }
+    h->own_label = true;
+    SW_CUDA(cudaMemsetAsync(h->d_label, 0, n, h->stream));
+    const Lattice self = h->lattice();
+    SW_CUDA(cudaMemcpyAsync(h->d_self, &self, sizeof self, cudaMemcpyHostToDevice, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->owner) h->owner->dirty = true;
+    return SW_OK;
+}
+
 // One sweep of batch view b on stream s, from a captured graph when asked.
 int enqueue_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape, cudaStream_t s,
                   bool use_graph, cudaGraph_t *graph, cudaGraphExec_t *exec)
@@ -441,7 +464,7 @@ std::string tune_key(int nrep, int ntasks, long long nmerge, bool measure)
 template <typename Timer>
 int autotune_shape(LaunchShape *best, int n, Timer timer)
 {
-    static const int cand_label[] = {4, 6, 8};
+    static const int cand_label[] = {6, 8, 10};
     static const int cand_other[] = {4, 8, 16, 32};
     double ms[swgb::kMaxStages];
     // Timed stages: 0 bonds, 1 labeling, 2 merge, 3 flip.
@@ -500,7 +523,8 @@ void free_handle(sw_handle *h)
     if (h->own_label && h->d_label) cudaFree(h->d_label);
     if (h->d_thr_tab) cudaFree(h->d_thr_tab);
     if (h->d_code) cudaFree(h->d_code);
-    if (h->d_open_list) cudaFree(h->d_open_list);
+    if (h->d_opar) cudaFree(h->d_opar);
+    if (h->d_edge) cudaFree(h->d_edge);
     if (h->d_open_count) cudaFree(h->d_open_count);
     if (h->d_cross) cudaFree(h->d_cross);
     if (h->d_R) cudaFree(h->d_R);
@@ -575,19 +599,17 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
         if ((e = cudaMalloc(&h->d_spin, N)) != cudaSuccess) return bail(e, "cudaMalloc(spins)");
         h->own_spin = true;
     }
-    if (d_labels) {
-        h->d_label = (int32_t *)d_labels;
-    } else {
-        if ((e = cudaMalloc(&h->d_label, N * sizeof(int32_t))) != cudaSuccess) return bail(e, "cudaMalloc(labels)");
-        h->own_label = true;
-    }
+    // The label array is only written with debug labels on or by a
+    // comparator labeling; it is allocated when one of them is enabled.
+    if (d_labels) h->d_label = (int32_t *)d_labels;
     if ((e = cudaMalloc(&h->d_st, sizeof(DevState))) != cudaSuccess) return bail(e, "cudaMalloc(state)");
     h->tiles_x = (L + swgb::kTileW - 1) / swgb::kTileW;
     h->tiles_y = (L + swgb::kTileH - 1) / swgb::kTileH;
     const size_t ntiles = (size_t)h->tiles_x * h->tiles_y;
     if ((e = cudaMalloc(&h->d_code, N * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(codes)");
-    if ((e = cudaMalloc(&h->d_open_list, ntiles * swgb::kOpenSlots * sizeof(int32_t))) != cudaSuccess)
-        return bail(e, "cudaMalloc(open roots)");
+    if ((e = cudaMalloc(&h->d_opar, ntiles * swgb::kOpenSlots * sizeof(unsigned long long))) != cudaSuccess)
+        return bail(e, "cudaMalloc(open components)");
+    if ((e = cudaMalloc(&h->d_edge, ntiles * swgb::kEdgeBytes)) != cudaSuccess) return bail(e, "cudaMalloc(edges)");
     if ((e = cudaMalloc(&h->d_open_count, ntiles * sizeof(int32_t))) != cudaSuccess)
         return bail(e, "cudaMalloc(open counts)");
     if ((e = cudaMalloc(&h->d_cross, ntiles * swgb::kCrossWords * sizeof(uint32_t))) != cudaSuccess)
@@ -644,7 +666,7 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
         return nullptr;
     }
     if ((e = cudaMemsetAsync(h->d_spin, 0, N, h->stream)) != cudaSuccess) return bail(e, "cudaMemset(spins)");
-    if ((e = cudaMemsetAsync(h->d_label, 0, N * sizeof(int32_t), h->stream)) != cudaSuccess)
+    if (h->d_label && (e = cudaMemsetAsync(h->d_label, 0, N * sizeof(int32_t), h->stream)) != cudaSuccess)
         return bail(e, "cudaMemset(labels)");
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "cudaStreamSynchronize");
     return h;
@@ -807,6 +829,11 @@ int sw_reset_stats(sw_handle *h)
 int sw_set_debug_labels(sw_handle *h, int on)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (on) {
+        int rc = drain(h);
+        if (rc == SW_OK) rc = ensure_labels(h);
+        if (rc != SW_OK) return rc;
+    }
     if (h->labels != (on != 0)) drop_graph(h);
     h->labels = on != 0;
     return SW_OK;
@@ -847,6 +874,7 @@ int sw_get_labels(sw_handle *h, int32_t *host, size_t n)
 {
     if (!h || !host) return fail(SW_ERR_ARG, "null argument");
     if (n != (size_t)h->L * h->L) return fail(SW_ERR_ARG, "n=%zu != L*L", n);
+    if (!h->d_label) return fail(SW_ERR_STATE, "no labels: turn debug labels on before sweeping");
     SW_CUDA(cudaMemcpyAsync(host, h->d_label, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     SW_CUDA(cudaStreamSynchronize(h->stream));
     return SW_OK;
@@ -993,6 +1021,8 @@ int sw_set_labeling(sw_handle *h, int method)
         if (!h->d_flag) SW_CUDA(cudaMalloc(&h->d_flag, sizeof(unsigned int)));
         if (!h->h_flag) SW_CUDA(cudaHostAlloc(&h->h_flag, sizeof(unsigned int), cudaHostAllocDefault));
         if (method == SW_LABEL_HAWICK && !h->d_R) SW_CUDA(cudaMalloc(&h->d_R, (size_t)h->L * h->L * sizeof(int32_t)));
+        rc = ensure_labels(h);
+        if (rc != SW_OK) return rc;
     }
     h->labeling = method;
     h->last_passes = 0;
@@ -1151,6 +1181,10 @@ int sw_batch_attach(sw_batch *b, sw_handle *h)
         drop_graph(h);
         h->measure = b->measure;
     }
+    if (b->labels) {
+        rc = ensure_labels(h);
+        if (rc != SW_OK) return rc;
+    }
     if (h->own_stream) cudaStreamDestroy(h->stream);
     h->own_stream = false;
     h->stream = b->stream;
@@ -1251,6 +1285,11 @@ int sw_batch_set_graph(sw_batch *b, int on)
 int sw_batch_set_debug_labels(sw_batch *b, int on)
 {
     if (!b) return fail(SW_ERR_ARG, "null batch");
+    if (on)
+        for (sw_handle *h : b->reps) {
+            int rc = ensure_labels(h);
+            if (rc != SW_OK) return rc;
+        }
     if (b->labels != (on != 0)) drop_batch_graph(b);
     b->labels = on != 0;
     return SW_OK;
@@ -1340,8 +1379,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the working buffers inside the shared array, sized for
 // the largest accepted lattice (SW_NOALLOC_MAX_L).
 struct NoallocLayout {
-    size_t label, code, open_list, open_count, cross, bond, ring, thr_tab, st, lat, task_off,
-        merge_off, ticket, total;
+    size_t code, opar, edge, open_count, cross, bond, ring, thr_tab, st, lat, task_off, merge_off, ticket, total;
 };
 constexpr int kNoallocRingSlots = 128;   // counter rows; longer calls are drained in chunks
 
@@ -1352,9 +1390,9 @@ constexpr NoallocLayout noalloc_layout()
                          ((SW_NOALLOC_MAX_L + swgb::kTileH - 1) / swgb::kTileH);
     NoallocLayout o{};
     size_t at = 0;
-    o.label = at;      at = align256(at + sites * sizeof(int32_t));
     o.code = at;       at = align256(at + sites * sizeof(uint16_t));
-    o.open_list = at;  at = align256(at + tiles * swgb::kOpenSlots * sizeof(int32_t));
+    o.opar = at;       at = align256(at + tiles * swgb::kOpenSlots * sizeof(unsigned long long));
+    o.edge = at;       at = align256(at + tiles * swgb::kEdgeBytes);
     o.open_count = at; at = align256(at + tiles * sizeof(int32_t));
     o.cross = at;      at = align256(at + tiles * swgb::kCrossWords * sizeof(uint32_t));
     o.bond = at;       at = align256(at + tiles * swgb::kBondWords * sizeof(uint32_t));
@@ -1439,9 +1477,10 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     lat.key0 = (uint32_t)(seed & 0xffffffffu);
     lat.key1 = (uint32_t)(seed >> 32);
     lat.spin = d_spins;
-    lat.label = (int32_t *)(base + kNoalloc.label);
+    lat.label = nullptr;   // no debug labels here
     lat.code = (uint16_t *)(base + kNoalloc.code);
-    lat.open_list = (int32_t *)(base + kNoalloc.open_list);
+    lat.opar = (unsigned long long *)(base + kNoalloc.opar);
+    lat.edge = base + kNoalloc.edge;
     lat.open_count = (int32_t *)(base + kNoalloc.open_count);
     lat.cross = (uint32_t *)(base + kNoalloc.cross);
     lat.bond = (uint32_t *)(base + kNoalloc.bond);

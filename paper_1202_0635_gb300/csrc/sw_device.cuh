@@ -38,9 +38,11 @@ struct Lattice {
     const uint32_t *thr_tab;    // clock: (2q) x (2q) thresholds by class
     uint32_t key0, key1;        // Philox key = seed
     int8_t *spin;               // L*L states
-    int32_t *label;             // L*L words: union-find parents of open tile roots; debug labels
+    int32_t *label;             // L*L canonical labels (debug labels and the comparator labelings only)
     uint16_t *code;             // L*L per-site codes written by the labeling stage
-    int32_t *open_list;         // tiles x kOpenSlots global indices of open tile roots
+    unsigned long long *opar;   // tiles x kOpenSlots: union-find over the open components of all tiles
+                                // (component id = tile * kOpenSlots + slot), entry = key << 32 | parent id
+    uint8_t *edge;              // tiles x kEdgeBytes: open slot of the right-edge sites, then the left-edge sites
     int32_t *open_count;        // tiles
     uint32_t *cross;            // tiles x kCrossWords: active crossing bonds (right edge rows, bottom edge columns)
     uint32_t *bond;             // tiles x 256 words: a tile's right-bond masks (64 rows x 2 words), then
@@ -113,56 +115,64 @@ __device__ __forceinline__ void record_error(DevState *st, int code, int where)
 }
 
 // ---------------------------------------------------------------------------
-// Global union-find over the label array.  Invariant: label[x] <= x, so the
-// root of every tree is its smallest element and chains strictly decrease
-// (a chase can never exceed the number of sites).  Roots are linked larger
-// under smaller with atomicMin; path halving writes only ancestors.
+// Global union-find over the open components of every tile (Sec. 2: the
+// "proper label" of a cluster is its smallest site).  Node x = tile *
+// kOpenSlots + slot; its entry holds its parent's key (the smallest site of
+// the parent's tile component) in the high word and the parent's id in the
+// low word, so entries order by key.  A root is its own parent.  Roots are
+// linked larger key under smaller with a 64-bit atomicMin, so the root of a
+// tree is its component with the smallest site; path halving writes only
+// ancestors.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int ld_volatile(const int32_t *p)
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long *p)
 {
-    return *reinterpret_cast<const volatile int32_t *>(p);
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
 }
 
-__device__ __forceinline__ int find_root_halving(int32_t *label, int x, int cap, DevState *st)
+// Root entry of node x (key << 32 | root id).
+__device__ __forceinline__ unsigned long long find_open(unsigned long long *par, uint32_t x, int cap, DevState *st)
 {
     const long long t0 = clock64();
     for (int it = 0; it < cap; ++it) {
-        const int p = ld_volatile(label + x);
-        if (p == x) return x;
-        const int gp = ld_volatile(label + p);
-        if (gp == p) return p;
-        label[x] = gp;   // ancestor of x: safe under concurrent linking
+        const unsigned long long e = ld_volatile64(par + x);
+        const uint32_t p = (uint32_t)e;
+        if (p == x) return e;
+        const unsigned long long ep = ld_volatile64(par + p);
+        const uint32_t gp = (uint32_t)ep;
+        if (gp == p) return ep;
+        par[x] = ep;   // grandparent: an ancestor of x, safe under concurrent linking
         x = gp;
         if ((it & 255) == 255 && clock64() - t0 > kLoopBudgetCycles) {
-            record_error(st, kErrTimeBudget, x);
-            return x;
+            record_error(st, kErrTimeBudget, (int)x);
+            return ld_volatile64(par + x);
         }
     }
-    record_error(st, kErrFindCap, x);
-    return x;
+    record_error(st, kErrFindCap, (int)x);
+    return ld_volatile64(par + x);
 }
 
-__device__ __forceinline__ void union_roots(int32_t *label, int a, int b, int cap, DevState *st)
+__device__ __forceinline__ void union_open(unsigned long long *par, uint32_t a, uint32_t b, int cap, DevState *st)
 {
     const long long t0 = clock64();
+    // Both entries in flight at once: most ends are roots already.
+    unsigned long long ea = ld_volatile64(par + a), eb = ld_volatile64(par + b);
+    if ((uint32_t)ea != a) ea = find_open(par, a, cap, st);
+    if ((uint32_t)eb != b) eb = find_open(par, b, cap, st);
     for (int it = 0; it < cap; ++it) {
-        // Both parents in flight at once: most ends are roots already.
-        const int pa = ld_volatile(label + a), pb = ld_volatile(label + b);
-        if (pa != a) a = find_root_halving(label, pa, cap, st);
-        if (pb != b) b = find_root_halving(label, pb, cap, st);
-        if (a == b) return;
-        const int hi = a > b ? a : b;
-        const int lo = a > b ? b : a;
-        const int old = atomicMin(label + hi, lo);
-        if (old == hi) return;          // hi was a root: now under lo
-        a = old;                        // hi had moved under old: join old and lo
-        b = lo;
+        if (ea == eb) return;
+        const unsigned long long hi = ea > eb ? ea : eb;
+        const unsigned long long lo = ea > eb ? eb : ea;
+        const unsigned long long old = atomicMin(par + (uint32_t)hi, lo);
+        if (old == hi) return;   // hi was a root: now under lo
+        // hi had been linked under old meanwhile: join old's tree and lo's.
+        ea = find_open(par, (uint32_t)old, cap, st);
+        eb = find_open(par, (uint32_t)lo, cap, st);
         if (clock64() - t0 > kLoopBudgetCycles) {
-            record_error(st, kErrTimeBudget, a);
+            record_error(st, kErrTimeBudget, (int)(uint32_t)hi);
             return;
         }
     }
-    record_error(st, kErrUnionCap, a);
+    record_error(st, kErrUnionCap, (int)a);
 }
 
 // A state outside [0, q) (only possible through a caller writing the spin
@@ -172,70 +182,53 @@ __device__ __forceinline__ int valid_state(int s, int q)
     return (unsigned)s < (unsigned)q ? s : 0;
 }
 
-// Shared-memory union-find over the nodes v = row * 64 + column of a tile
-// (same invariants), one 16-bit parent word per node.  Node v lives in slot
-// v ^ (row & 31): the same column of different rows falls in different
-// banks.  The map is its own inverse.  Parent words below kTileResolved
-// are nodes; a word >= kTileResolved marks a root whose cluster is settled
-// (it carries the cluster's code).
+// Shared-memory union-find of a tile over its nodes v = row * 64 + column,
+// one 16-bit word per node (same invariants: a word is never above its
+// node, larger root linked under smaller, so a root is its component's
+// smallest node).  A link is one 16-bit compare-and-swap that succeeds only
+// while the larger root is still a root.  After the roots are settled, a
+// root's word is kTileResolved | its cluster's code.
 constexpr int kTileResolved = 0x1000;
-
-__device__ __forceinline__ int tile_slot(int v)
-{
-    return v ^ ((v >> 6) & 31);
-}
-
-__device__ __forceinline__ int par_ld(const volatile uint16_t *par, int v)
-{
-    return par[tile_slot(v)];
-}
 
 // Root of x with path halving (writes only ancestors).  Valid while no word
 // is resolved.  Returns -1 if the cap is exceeded.
 __device__ __forceinline__ int find_t(volatile uint16_t *par, int x, int cap)
 {
     for (int it = 0; it < cap; ++it) {
-        const int p = par_ld(par, x);
+        const int p = par[x];
         if (p == x) return x;
-        const int gp = par_ld(par, p);
+        const int gp = par[p];
         if (gp == p) return p;
-        par[tile_slot(x)] = (uint16_t)gp;
+        par[x] = (uint16_t)gp;
         x = gp;
     }
     return -1;
 }
 
-// Link root hi under lo if hi is still a root; returns hi's parent word as
-// it was (== hi on success).  A compare-and-swap on the 32-bit word that
-// holds the 16-bit slot.
-__device__ __forceinline__ int link_t(volatile uint16_t *par, int hi, int lo)
+// Root of x without writing.
+__device__ __forceinline__ int find_t_ro(const volatile uint16_t *par, int x, int cap)
 {
-    const int s = tile_slot(hi);
-    unsigned int *w = (unsigned int *)(par) + (s >> 1);
-    const int sh = 16 * (s & 1);
-    unsigned int old = *(volatile unsigned int *)w;
-    for (;;) {
-        const int cur = (int)((old >> sh) & 0xFFFFu);
-        if (cur != hi) return cur;
-        const unsigned int nw = (old & ~(0xFFFFu << sh)) | ((unsigned int)lo << sh);
-        const unsigned int seen = atomicCAS(w, old, nw);
-        if (seen == old) return hi;
-        old = seen;
+    for (int it = 0; it < cap; ++it) {
+        const int p = par[x];
+        if (p == x) return x;
+        x = p;
     }
+    return -1;
 }
 
 __device__ __forceinline__ bool union_t(volatile uint16_t *par, int a, int b, int cap)
 {
     for (int it = 0; it < cap; ++it) {
         // Both parents in flight at once: the ends are often roots.
-        const int pa = par_ld(par, a), pb = par_ld(par, b);
+        const int pa = par[a], pb = par[b];
         if (pa != a) a = find_t(par, pa, cap);
         if (pb != b) b = find_t(par, pb, cap);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
         const int hi = a > b ? a : b;
         const int lo = a > b ? b : a;
-        const int old = link_t(par, hi, lo);
+        const int old = atomicCAS(const_cast<unsigned short *>(reinterpret_cast<volatile unsigned short *>(par)) + hi,
+                                  (unsigned short)hi, (unsigned short)lo);
         if (old == hi) return true;
         a = old;   // hi was linked meanwhile: join its new parent and lo
         b = lo;

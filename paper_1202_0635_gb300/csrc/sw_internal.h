@@ -22,6 +22,11 @@ static_assert(kTaskWarps == (kTileW / kQuad) * (kTileH / kQuad), "one warp per q
 // A component that reaches a tile border ("open") owns a border site, so a
 // tile has at most 2 * (W + H) - 4 = 252 open components.
 constexpr int kOpenSlots = 256;
+// Edge bytes per tile: the open slot of the component of each right-edge
+// site (rows 0..63), then of each left-edge site.  The merge stage reads
+// them for the crossing bonds; the bottom and top edges are read from the
+// codes, which are contiguous there.
+constexpr int kEdgeBytes = 128;
 // Crossing-bond words per tile: [0], [1] bit r = right-edge bond of row
 // 32 * w + r; [2], [3] bit c = bottom-edge bond of column 32 * w + c.
 constexpr int kCrossWords = 4;
@@ -53,7 +58,7 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
 // labeling, merge, flip and bond kernels (the grids never exceed the work).
 // Any shape gives the same results; only the speed differs.
 struct LaunchShape {
-    int label = 8, merge = 16, flip = 10, bonds = kBondBlocksPerSM;
+    int label = 10, merge = 16, flip = 10, bonds = kBondBlocksPerSM;
 };
 // ev (optional): events recorded before the first and after every kernel of
 // the sweep (kMaxStages + 1 entries): bonds, labeling, merge, flip.

@@ -40,12 +40,6 @@ constexpr int TW = kTileW, TH = kTileH, NS = kTileSites, QW = kQuad;
 constexpr int kBlockThreads = kTaskWarps * 32;
 constexpr int kEnergyThreads = 256;
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kInfLabel = 1 << 20;      // "no label" (larger than any tile node)
-// Queued unions per tile (a row of a quadrant makes at most 31 requests;
-// random bonds make about 260 a tile at T_c).  A tile whose requests exceed
-// the queue joins all its internal bonds after the scan instead.
-constexpr int kMaxPairs = 2048;
-constexpr int kFreshList = 2 * kMaxPairs;  // fresh labels listed per tile (more: settled in place)
 // Resident blocks per SM of the flip kernel's variants (its launch bounds);
 // its grid never asks for more, so that one wave covers the tiles.
 constexpr int kFlipResidentPotts = 10, kFlipResidentClock = 8;
@@ -111,10 +105,6 @@ __device__ __forceinline__ int byte_at(const uint32_t (&w)[8], int c)
 {
     return (int)((w[c >> 2] >> (8 * (c & 3))) & 0xFFu);
 }
-
-// Union of labels a and b, queued in slot idx of the tile's list, or done at
-// once when the list is full.
-
 
 __device__ __forceinline__ int reflect(int k, int m, int q)
 {
@@ -555,44 +545,87 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
     flush();
 }
 
-// Every bond inside a tile joined in the shared union-find: the fallback of
-// a tile whose union requests overflow the queue.  rowR / rowD hold the
-// tile-internal right and down bonds of each row (two 32-bit halves).
-__device__ __noinline__ void join_tile_bonds(volatile uint16_t *par, const uint16_t *lbl,
-                                             const unsigned int (*rowR)[2], const unsigned int (*rowD)[2], int tw,
-                                             int th, DevState *st, int where)
+// Segmented prefix OR: bit c of the result is the OR of the bits of x from
+// the start of c's segment up to c; segments start at the set bits of m and
+// at bit 0.  Five doubling steps.
+__device__ __forceinline__ unsigned seg_or(unsigned x, unsigned m)
 {
-    for (int item = threadIdx.x; item < 2 * kTileSites; item += blockDim.x) {
-        const int node = item >> 1, down = item & 1;
-        const int r = node / kTileW, c = node % kTileW;
-        if (r >= th || c >= tw) continue;
-        const unsigned bits = down ? rowD[r][c >> 5] : rowR[r][c >> 5];
-        if (!((bits >> (c & 31)) & 1u)) continue;
-        const int other = down ? node + kTileW : node + 1;
-        if (!union_t(par, lbl[node], lbl[other], kTileSites + 1)) record_error(st, kErrUnionCap, where);
+    unsigned p = ~m & ~1u;   // bit c may receive from bit c - 1
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+        x |= (x << sh) & p;
+        p &= p << sh;
     }
-    __syncthreads();
+    return x;
 }
+
+// Bit c is set iff bit c of x is set and no lower bit of x lies in c's
+// segment (segments as above).
+__device__ __forceinline__ unsigned seg_first(unsigned x, unsigned m)
+{
+    return x & ~((seg_or(x, m) << 1) & ~m);
+}
+
+// Run start at or left of column c (0..31) in a row's run-start word.
+__device__ __forceinline__ int run_start(unsigned s, int c)
+{
+    return 31 - __clz(s & (FULL >> (31 - c)));
+}
+
+// Per quadrant row, for the scan: run starts, the first down bond from the
+// row above into each run ("hook"), and the starts of the hooked runs.
+// D: the row's down bonds inside the tile (for the seam between quadrants).
+struct RowMasks {
+    unsigned S, H, HS, D;
+};
 
 // ---------------------------------------------------------------------------
 // k_label_tiles
 //
-// Per quadrant (warp), lane r holds row r's bond masks.  Phase B labels the
-// quadrant row by row (lane = column); queued unions, the seams between
-// quadrants and every label's root are then resolved in shared memory,
-// components that reach the tile border are marked open, closed roots draw,
-// and each site's code is written.
+// One block labels one 64 x 64 tile; warp w owns the 32 x 32 quadrant
+// (qx, qy) = (w & 1, w >> 1).
+//   masks    (lane = row) runs are the maximal horizontally bonded segments
+//            of a quadrant row, found with bit operations: run starts, the
+//            first down bond reaching each run from the row above (its
+//            hook), and every further down bond that is the first to join a
+//            distinct pair of runs.
+//   scan     (lane = column, row by row, as in Hoshen-Kopelman, Sec. 2) a
+//            hooked run takes the provisional label of the site above its
+//            hook; any other run opens a provisional label, its first node
+//            (tile node row * 64 + column, ordered like site indices).
+//            Every node's word holds its provisional label; for the first
+//            node of a run that opened one, that is the node itself, so the
+//            same words serve as the union-find parents of the labels.
+//   unions   the further down bonds, the quadrant seams (column 31 | 32,
+//            row 31 | 32) join provisional labels in that union-find,
+//            larger root under smaller, so a component's root is its
+//            smallest site.
+//   open     a component reaching the tile border (left and top edges
+//            always, right and bottom edges through an active crossing
+//            bond) continues in the neighbouring tile.
+//   settle   every provisional label points at its root; a closed root
+//            draws its cluster's new state (Sec. 2 steps (v)-(vii); clock:
+//            the reflection flag, Sec. 4); an open root takes a slot and
+//            becomes a node of the global union-find.
+//   codes    every site gets its cluster's 2-byte code, 0x100 | new state
+//            (closed Potts), 0x100 | reflection flag (closed clock) or the
+//            open slot; the open slots of the right and left edge sites go
+//            to the tile's edge bytes.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
+__global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
 {
-    __shared__ __align__(16) uint16_t par[NS];     // union-find over labels, node v in slot tile_slot(v)
-    __shared__ __align__(16) uint16_t lbl[NS];     // label of every node at its row's scan
-    __shared__ __align__(16) uint32_t upairs[kMaxPairs];   // queued unions; then the list of roots
-    __shared__ __align__(8) unsigned int rowR[TH][2], rowD[TH][2];
-    __shared__ unsigned int openw[NS / 32];
-    __shared__ int rmin_all[kTaskWarps][QW];                // per-warp run minima of the scan
-    __shared__ int s_nopen, s_npairs, s_wsum[kTaskWarps];
+    // Node words: provisional label of every node, which for a label's own
+    // first node is its union-find parent.
+    __shared__ __align__(16) uint16_t X[NS];
+    // The union pairs (provisional labels of both ends, packed in a word);
+    // then the list of provisional labels.
+    __shared__ __align__(16) uint16_t rlist[NS];
+    uint32_t *ulist = reinterpret_cast<uint32_t *>(rlist);
+    constexpr int kUnionList = NS / 2;
+    __shared__ __align__(16) RowMasks sm[TH][2];      // scan masks by (row, half)
+    __shared__ unsigned int openw[NS / 32];           // open roots
+    __shared__ int s_nroots, s_nopen, s_npairs;
     __shared__ unsigned int s_cross[kCrossWords];
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
@@ -600,6 +633,7 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qx = warp & 1, qy = warp >> 1;
+    const int row = QW * qy + lane;   // my tile row (lane = row phases)
 
     unsigned int closed_roots = 0;
     int cur = -1;
@@ -631,295 +665,244 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
         const int ncols = max(0, min(QW, tw - QW * qx));
         const int nrows = max(0, min(QW, th - QW * qy));
         const bool qa = ncols > 0 && nrows > 0;                        // quadrant has sites (warp-uniform)
+        const bool rv = qa && lane < nrows;                            // my row has sites
         const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
         const bool ext_right = QW * qx + ncols == tw;                   // my right edge is the tile's
         const bool ext_bottom = QW * qy + nrows == th;
-        unsigned rc_bits = 0, dc_bits = 0;
-        unsigned Rq = 0, Dq = 0;   // lane r: row r's bonds inside the quadrant (right, down)
 
-        for (int i = threadIdx.x; i < NS / 32; i += blockDim.x) openw[i] = 0u;
-        if (threadIdx.x == 0) s_nopen = 0;
-        if (threadIdx.x == 0) s_npairs = 0;
-
-        // ===== bond masks of my quadrant (written by k_bonds), lane = row ======
-        if (qa) {
-            const int r = lane;
-            const bool rv = r < nrows;
-            const uint32_t *tb = lat.bond + (size_t)tile * kBondWords + (QW * qy + r) * 2 + qx;
+        // ===== masks (lane = row; bond masks written by k_bonds) ================
+        unsigned S = 0u, U2 = 0u;
+        bool seam = false;
+        {
+            const uint32_t *tb = lat.bond + (size_t)tile * kBondWords + row * 2 + qx;
             const unsigned R = rv ? __ldg(tb) : 0u;
             const unsigned D = rv ? __ldg(tb + kBlockThreads) : 0u;
-            rc_bits = __ballot_sync(FULL, rv && ((R >> (ncols - 1)) & 1u));   // bonds leaving the right edge
-            dc_bits = __shfl_sync(FULL, D, nrows - 1);                       // bonds leaving the bottom edge
-            // Tile-internal bonds as 64-bit rows (two 32-bit halves): the
-            // right bond of the tile's last column and the down bonds of its
-            // last row cross into the neighbouring tiles.
-            const unsigned Rin = R & (ext_right ? (V >> 1) : V);
-            const unsigned Din = (ext_bottom && r == nrows - 1) ? 0u : D;
-            rowR[QW * qy + r][qx] = rv ? Rin : 0u;
-            rowD[QW * qy + r][qx] = rv ? Din : 0u;
-            Rq = rv ? (R & (V >> 1)) : 0u;             // both ends in the quadrant
-            Dq = (r + 1 < nrows) ? D : 0u;
-            if (lane == 0) {
-                if (ext_right) atomicOr(&s_cross[qy], rc_bits);
-                if (ext_bottom) atomicOr(&s_cross[2 + qx], dc_bits);
+            if (qa) {
+                const unsigned rc_bits = __ballot_sync(FULL, rv && ((R >> (ncols - 1)) & 1u));   // leaving the right edge
+                const unsigned dc_bits = __shfl_sync(FULL, D, nrows - 1) & V;                   // leaving the bottom edge
+                if (lane == 0) {
+                    if (ext_right) atomicOr(&s_cross[qy], rc_bits);
+                    if (ext_bottom) atomicOr(&s_cross[2 + qx], dc_bits);
+                }
             }
-        } else {
-            rowR[QW * qy + lane][qx] = 0u;
-            rowD[QW * qy + lane][qx] = 0u;
+            const unsigned Rq = R & (V >> 1);                // right bonds with both ends in the quadrant
+            S = rv ? (~(Rq << 1) & V) : 0u;                  // run starts (column 0 always starts one)
+            const unsigned Din = (rv && row + 1 < th) ? (D & V) : 0u;   // down bonds inside the tile
+            // Down bonds from the row above, inside the quadrant.
+            const unsigned Dup = __shfl_up_sync(FULL, Din, 1);
+            const unsigned Sp = __shfl_up_sync(FULL, S, 1);
+            const unsigned Dp = lane > 0 ? Dup : 0u;
+            const unsigned H = seg_first(Dp, S);                              // hook of each run
+            const unsigned E = (S >> 1) | 0x80000000u;                        // run ends
+            const unsigned HS = S & __brev(seg_or(__brev(Dp), __brev(E)));    // starts of hooked runs
+            U2 = rv ? (seg_first(Dp, S | Sp) & ~H) : 0u;                      // further run pairs
+            seam = rv && qx == 0 && tw > QW && ((R >> 31) & 1u);             // column 31 -> 32
+            sm[row][qx] = RowMasks{S, H, HS, Din};
         }
+        openw[threadIdx.x] = 0u;
+        static_assert(NS / 32 == kBlockThreads, "one open word per thread");
+        if (threadIdx.x == 0) s_nroots = s_nopen = s_npairs = 0;
         __syncthreads();
 
-        // ===== labels, quadrant by quadrant (warp), lane = column ===============
-        // Row by row, every site carries the label of the site above it when
-        // the two are bonded.  A run (maximal horizontally bonded segment of
-        // the row) takes the label carried by its first such site; a run with
-        // none opens a fresh label, its first node.  Other labels carried into
-        // the run are queued for a union with the run's.  Labels are tile
-        // nodes row * 64 + column, which order like global site indices, so
-        // with unions linking larger roots under smaller each component's
-        // root is its smallest site.
+        // ===== scan (lane = column): provisional labels row by row ============
+        // Four rows per step (nrows % 4 == 0): their mask work is independent
+        // and overlaps the chain through lab.
         if (qa) {
             const int c = lane;
-            const bool cv = c < ncols;
-            const unsigned bit = 1u << c;
-            const unsigned upto = FULL >> (31 - c);   // columns <= c
-            const int nb = (QW * qy) * TW + QW * qx;  // node of the quadrant's corner
-            int *rmin = rmin_all[warp];
-            int pl = 0;                               // label of the site above (valid where Dp has my bit)
-            uint32_t lastq = 0xFFFFFFFFu;             // pair this lane queued last
-            unsigned Dp = 0u, Rp = 0u;
-            for (int row = 0; row < nrows; ++row) {
-                const unsigned Rr = __shfl_sync(FULL, Rq, row);
-                const unsigned S = ~(Rr << 1);                       // run starts
-                const int s0 = 31 - __clz(S & upto);                 // my run's first column
-                // The run takes the smallest label a bond from above carries
-                // into it (collected at its first column), else a fresh
-                // label: its first node.
-                rmin[c] = kInfLabel;
-                __syncwarp();
-                if (Dp & bit) atomicMin(&rmin[s0], pl);
-                __syncwarp();
-                const int node = nb + row * TW + c;
-                const int up = rmin[s0];
-                const int mlab = up != kInfLabel ? up : node - (c - s0);
-                if (cv) {
-                    if (mlab == node) par[node ^ row] = (uint16_t)node;   // tile_slot(node): row < 32
-                    lbl[node] = (uint16_t)mlab;
+            int lab = 0;
+            uint16_t *pl = X + QW * qy * TW + QW * qx + c;
+            for (int r0 = 0; r0 < nrows; r0 += 4) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int r = r0 + j;
+                    const RowMasks m = sm[QW * qy + r][qx];
+                    const int s0 = run_start(m.S, c);
+                    const bool hooked = (m.HS >> s0) & 1u;
+                    const int fc = s0 + __ffs(m.H >> s0) - 1;
+                    const int up = __shfl_sync(FULL, lab, fc & 31);
+                    lab = hooked ? up : (QW * qy + r) * TW + QW * qx + s0;
+                    pl[r * TW] = (uint16_t)lab;
                 }
-                // A bond from above carrying another label queues a union,
-                // unless its left neighbour joins the same two runs or this
-                // lane queued the same pair last.
-                const unsigned E = Dp & ~((Dp & Rp & Rr) << 1);
-                const uint32_t pair = (uint32_t)pl | ((uint32_t)mlab << 16);
-                const bool u = (E & bit) && pl != mlab && pair != lastq;
-                if (u) {   // a slot of its own: no warp vote on the row's path
-                    const int idx = atomicAdd(&s_npairs, 1);
-                    if (idx < kMaxPairs) upairs[idx] = pair;
-                    lastq = pair;
-                }
-                __syncwarp();
-                pl = mlab;
-                Rp = Rr;
-                Dp = __shfl_sync(FULL, Dq, row);
             }
         }
         __syncthreads();
 
-        // A queue overflow (block-uniform): join every bond inside the tile.
-        if (s_npairs > kMaxPairs) join_tile_bonds(par, lbl, rowR, rowD, tw, th, lat.st, Y0 * L + X0);
-
-        // ===== unions: queued pairs, then the seams between the quadrants =====
+        // ===== unions: further run pairs and the quadrant seams ===============
+        // Each lane (row) lists its pairs of provisional labels: further down
+        // bonds from the row above, the right bond across column 31 | 32 and,
+        // for row 32, the down bonds across row 31 | 32 of its half.  All
+        // threads then join the listed pairs; pairs beyond the list's room
+        // are joined by their lane.
         {
-            const int np = min(s_npairs, kMaxPairs);
-            const int nitems = np + TH + TW;
-            for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
-                int a, c;
-                if (i < np) {
-                    const uint32_t pr = upairs[i];
-                    a = (int)(pr & 0xFFFFu);
-                    c = (int)(pr >> 16);
-                } else if (i < np + TH) {   // column 31 - 32 of row y
-                    const int y = i - np;
-                    if (y >= th || tw <= QW || !((rowR[y][0] >> 31) & 1u)) continue;
-                    a = lbl[y * TW + QW - 1];
-                    c = lbl[y * TW + QW];
-                } else {                     // row 31 - 32 of column x
-                    const int x = i - np - TH;
-                    if (x >= tw || th <= QW || !((rowD[QW - 1][x >> 5] >> (x & 31)) & 1u)) continue;
-                    a = lbl[(QW - 1) * TW + x];
-                    c = lbl[QW * TW + x];
+            const int nb = row * TW + QW * qx;
+            // Row 31 | 32 of my half: lane = column, one pair per lane at most.
+            bool fs = false;
+            if (qy == 1 && qa) {
+                const RowMasks above = sm[QW - 1][qx], below = sm[QW][qx];
+                fs = (seg_first(above.D, above.S | below.S) >> lane) & 1u;
+            }
+            const int cnt = __popc(U2) + (int)fs + (int)seam;
+            int incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(FULL, incl, d);
+                if (lane >= d) incl += o;
+            }
+            int wbase = 0;
+            if (lane == 31 && incl) wbase = atomicAdd(&s_npairs, incl);
+            int at = __shfl_sync(FULL, wbase, 31) + incl - cnt;
+            // Slots of pairs found redundant stay at 0 | 0 (a no-op union).
+            // A pair whose two labels are already the same needs no union.
+            auto put = [&](int a, int bn) {
+                const uint32_t la = (uint32_t)X[a], lb = (uint32_t)X[bn];
+                const uint32_t pr = la == lb ? 0u : (la | (lb << 16));
+                if (at < kUnionList) {
+                    ulist[at] = pr;
+                } else if (!union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), NS + 1)) {
+                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
                 }
-                if (!union_t(par, a, c, NS + 1)) record_error(lat.st, kErrUnionCap, Y0 * L + X0);
+                ++at;
+            };
+            while (U2) {   // the site above and the site itself
+                const int c = __ffs(U2) - 1;
+                U2 &= U2 - 1;
+                put(nb - TW + c, nb + c);
+            }
+            if (fs) put((QW - 1) * TW + QW * qx + lane, QW * TW + QW * qx + lane);
+            if (seam) put(nb + QW - 1, nb + QW);
+        }
+        __syncthreads();
+        {
+            const int np = min(s_npairs, kUnionList);
+            for (int i0 = 0; i0 < np; i0 += blockDim.x) {   // uniform trip count: warp-wide dedup
+                const int i = i0 + threadIdx.x;
+                const uint32_t pr = i < np ? ulist[i] : 0u;
+                const unsigned peers = __match_any_sync(FULL, pr);
+                if (pr != 0u && (__ffs(peers) - 1) == lane &&
+                    !union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), NS + 1))
+                    record_error(lat.st, kErrUnionCap, Y0 * L + X0);
             }
         }
         __syncthreads();
 
-        // ===== fresh labels into one list; components reaching the border ======
-        // Fresh labels are the nodes that are their own label.  Thread t owns
-        // nodes 32 t .. 32 t + 31 (row t / 2).
-        unsigned fresh = 0;
-        {
-            const int vrow = threadIdx.x >> 1, vcol = 32 * (threadIdx.x & 1);
-            if (vrow < th && vcol < tw) {
-                const uint4 *lp = reinterpret_cast<const uint4 *>(lbl) + 4 * threadIdx.x;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint4 w4 = lp[k];
-                    const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int j = 8 * k + 2 * h;
-                        const uint32_t v = 32u * threadIdx.x + (uint32_t)j;
-                        fresh |= ((unsigned)((ws[h] & 0xFFFFu) == v) << j) | ((unsigned)((ws[h] >> 16) == v + 1u) << (j + 1));
-                    }
-                }
-                const int ncol = min(32, tw - vcol);
-                fresh &= ncol >= 32 ? FULL : ((1u << ncol) - 1u);
-            }
-        }
-        // Left and top edges always make a component open (their bonds belong
-        // to the neighbouring tiles); right and bottom edges through an active
-        // crossing bond.  Items: top row, left column, right column, bottom row.
+        // ===== open components: left and top edges always, right and bottom
+        // edges through an active crossing bond.  Items: left column, top
+        // row, right column, bottom row.  Also: the provisional labels listed.
         for (int item = threadIdx.x; item < 4 * TW; item += blockDim.x) {
             const int side = item / TW, k = item % TW;
             int node = -1;
             if (side == 0) {
-                if (k < tw) node = k;
-            } else if (side == 1) {
                 if (k < th) node = k * TW;
+            } else if (side == 1) {
+                if (k < tw) node = k;
             } else if (side == 2) {
                 if (k < th && ((s_cross[k >> 5] >> (k & 31)) & 1u)) node = k * TW + tw - 1;
             } else {
                 if (k < tw && ((s_cross[2 + (k >> 5)] >> (k & 31)) & 1u)) node = (th - 1) * TW + k;
             }
-            if (node < 0) continue;
-            const int root = find_t(par, lbl[node], NS + 1);
-            if (root < 0) {
-                record_error(lat.st, kErrFindCap, Y0 * L + X0);
-                continue;
+            int rt = -1;
+            if (node >= 0) {
+                rt = find_t_ro(X, X[node], NS + 1);
+                if (rt < 0) record_error(lat.st, kErrFindCap, Y0 * L + X0);
             }
-            atomicOr(&openw[root >> 5], 1u << (root & 31));
+            const unsigned peers = __match_any_sync(FULL, rt);   // one atomic per distinct root
+            if (rt >= 0 && (__ffs(peers) - 1) == lane) atomicOr(&openw[rt >> 5], 1u << (rt & 31));
         }
-        const int nmine = __popc(fresh);
-        int incl = nmine;
+        {   // provisional labels: the first nodes of the runs that opened one
+            const unsigned F = S & ~sm[row][qx].HS;
+            const int cnt = __popc(F);
+            int incl = cnt;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int o = __shfl_up_sync(FULL, incl, d);
-            if (lane >= d) incl += o;
-        }
-        if (lane == 31) s_wsum[warp] = incl;
-        __syncthreads();
-        int nfresh = 0, off = incl - nmine;
-#pragma unroll
-        for (int w = 0; w < kTaskWarps; ++w) {
-            off += w < warp ? s_wsum[w] : 0;
-            nfresh += s_wsum[w];
-        }
-        const bool listed = nfresh <= kFreshList;   // block-uniform
-        uint16_t *flist = reinterpret_cast<uint16_t *>(upairs);
-        if (listed) {
-            unsigned f2 = fresh;
-            while (f2) {
-                const int bit = __ffs(f2) - 1;
-                f2 &= f2 - 1;
-                flist[off++] = (uint16_t)(32 * threadIdx.x + bit);
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(FULL, incl, d);
+                if (lane >= d) incl += o;
             }
+            int wbase = 0;
+            if (lane == 31 && incl) wbase = atomicAdd(&s_nroots, incl);
+            int at = __shfl_sync(FULL, wbase, 31) + incl - cnt;
+            const int nb = row * TW + QW * qx;
+            for (unsigned f = F; f; f &= f - 1) rlist[at++] = (uint16_t)(nb + __ffs(f) - 1);
         }
         __syncthreads();
 
-        // ===== settle: roots draw (closed) or take an open slot; every other
-        // fresh label is pointed straight at its root.  A root's parent word
-        // becomes resolved (it carries the outcome).
-        auto settle = [&](int v) {
-            int x = v;
-            for (int it = 0; it <= NS; ++it) {   // read-only chase: stops at a root, settled or not
-                const int p = par_ld(par, x);
-                if (p == x || p >= kTileResolved) break;
-                x = p;
-            }
-            if (x != v) {
-                par[tile_slot(v)] = (uint16_t)x;
-                return;
-            }
-            const int g = tile_site(L, bx, by, v);
-            int w;
-            if ((openw[v >> 5] >> (v & 31)) & 1u) {
-                const int slot = atomicAdd(&s_nopen, 1);
-                if (slot < kOpenSlots) {   // at most 2 * (64 + 64) - 4 open components
-                    lat.open_list[(size_t)tile * kOpenSlots + slot] = g;
-                    lat.label[g] = g;
-                    w = kTileResolved | slot;
-                } else {
-                    record_error(lat.st, kErrInternal, g);
-                    w = kTileResolved | kCodeClosed;
+        // ===== settle: every provisional label points at its root; a closed
+        // root draws, an open root takes a slot.  A settled root's word is
+        // resolved; walks stop there.
+        {
+            const int nlab = s_nroots;
+            for (int i = threadIdx.x; i < nlab; i += blockDim.x) {
+                const int v = rlist[i];
+                int x = v;
+                for (int it = 0; it <= NS; ++it) {   // read-only: stops at a root, settled or not
+                    const int p = X[x];
+                    if (p == x || p >= kTileResolved) break;
+                    x = p;
                 }
-            } else {
-                const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
-                w = kTileResolved | kCodeClosed | (clock ? (int)(u >> 31) : mulhi_q(u, q));
-                ++closed_roots;
-            }
-            par[tile_slot(v)] = (uint16_t)w;
-        };
-        if (listed) {
-            for (int i = threadIdx.x; i < nfresh; i += blockDim.x) settle(flist[i]);
-        } else {
-            unsigned f2 = fresh;
-            while (f2) {
-                const int bit = __ffs(f2) - 1;
-                f2 &= f2 - 1;
-                settle(32 * threadIdx.x + bit);
-            }
-        }
-        __syncthreads();
-        // Every other fresh label takes its root's resolved word, so that a
-        // site's label leads to its outcome in one step.  The roots' words
-        // are only read here.  (Debug labels keep the root's index instead.)
-        auto adopt = [&](int v) {
-            const int p = par_ld(par, v);
-            if (p < kTileResolved) par[tile_slot(v)] = (uint16_t)par_ld(par, p);
-        };
-        if (LABELS) {
-        } else if (listed) {
-            for (int i = threadIdx.x; i < nfresh; i += blockDim.x) adopt(flist[i]);
-        } else {
-            while (fresh) {
-                const int bit = __ffs(fresh) - 1;
-                fresh &= fresh - 1;
-                adopt(32 * threadIdx.x + bit);
+                if (x != v) {
+                    X[v] = (uint16_t)x;
+                    continue;
+                }
+                const int g = tile_site(L, bx, by, v);
+                int w;
+                if ((openw[v >> 5] >> (v & 31)) & 1u) {
+                    const int slot = atomicAdd(&s_nopen, 1);
+                    if (slot < kOpenSlots) {   // at most 2 * (64 + 64) - 4 open components
+                        const uint32_t id = (uint32_t)tile * kOpenSlots + (uint32_t)slot;
+                        lat.opar[id] = ((unsigned long long)(uint32_t)g << 32) | id;
+                        w = kTileResolved | slot;
+                    } else {
+                        record_error(lat.st, kErrInternal, g);
+                        w = kTileResolved | kCodeClosed;
+                    }
+                } else {
+                    const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
+                    w = kTileResolved | kCodeClosed | (clock ? (int)(u >> 31) : mulhi_q(u, q));
+                    ++closed_roots;
+                }
+                X[v] = (uint16_t)w;
             }
         }
         __syncthreads();
 
-        // ===== codes: lane = four columns, two rows per warp step ==============
-        const int c4 = 4 * (lane & 15);
-        if (c4 < tw) {   // tw % 4 == 0: all four columns or none
-            for (int row = 2 * warp + (lane >> 4); row < th; row += 2 * kTaskWarps) {
-                const uint2 lp = reinterpret_cast<const uint2 *>(lbl)[(row * TW + c4) >> 2];
-                int xn[4] = {(int)(lp.x & 0xFFFFu), (int)(lp.x >> 16), (int)(lp.y & 0xFFFFu), (int)(lp.y >> 16)};
-                int w[4];
+        // ===== codes: warp = quadrant, four rows of 32 columns a step, lane =
+        // four columns; a node's word leads to its cluster's resolved word in
+        // at most two more steps (label -> root).  Edge slots.
+        if (qa) {
+            const int c4 = 4 * (lane & 7);
+            const bool cv = c4 < ncols;   // ncols % 4 == 0
+            for (int r = lane >> 3; r < nrows; r += 4) {
+                const int row2 = QW * qy + r;
+                const int v0 = row2 * TW + QW * qx + c4;
+                if (!cv) continue;
+                const uint2 w2 = *reinterpret_cast<const uint2 *>(X + v0);
+                int wv[4] = {(int)(w2.x & 0xFFFFu), (int)(w2.x >> 16), (int)(w2.y & 0xFFFFu), (int)(w2.y >> 16)};
+                int rt[4] = {v0, v0 + 1, v0 + 2, v0 + 3};
+                // label -> root -> resolved word: two rounds of independent loads
 #pragma unroll
-                for (int k = 0; k < 4; ++k) w[k] = par_ld(par, xn[k]);
-                if (LABELS) {   // a label's word is resolved (a root) or names its root
+                for (int it = 0; it < 2; ++it) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (w[k] < kTileResolved) {
-                            xn[k] = w[k];
-                            w[k] = par_ld(par, w[k]);
+                    for (int h = 0; h < 4; ++h)
+                        if (wv[h] < kTileResolved) {
+                            rt[h] = wv[h];
+                            wv[h] = X[wv[h]];
                         }
                 }
-                if (!(w[0] & w[1] & w[2] & w[3] & kTileResolved)) {   // unreachable for a settled tile
+                if (!(wv[0] & wv[1] & wv[2] & wv[3] & kTileResolved)) {   // unreachable for a settled tile
                     record_error(lat.st, kErrInternal, Y0 * L + X0);
-                    w[0] = w[1] = w[2] = w[3] = kTileResolved | kCodeClosed;
+                    wv[0] = wv[1] = wv[2] = wv[3] = kTileResolved | kCodeClosed;
                 }
-                const size_t site = (size_t)(Y0 + row) * L + X0 + c4;
-                const uint2 codes = make_uint2(((uint32_t)w[0] | ((uint32_t)w[1] << 16)) & (kCodeMask * 0x10001u),
-                                               ((uint32_t)w[2] | ((uint32_t)w[3] << 16)) & (kCodeMask * 0x10001u));
+                const size_t site = (size_t)(Y0 + row2) * L + X0 + QW * qx + c4;
+                *reinterpret_cast<uint2 *>(lat.code + site) =
+                    make_uint2(((uint32_t)wv[0] & kCodeMask) | (((uint32_t)wv[1] & kCodeMask) << 16),
+                               ((uint32_t)wv[2] & kCodeMask) | (((uint32_t)wv[3] & kCodeMask) << 16));
                 if (LABELS) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (w[k] & kCodeClosed) lat.label[site + k] = tile_site(L, bx, by, xn[k]);
+                    for (int h = 0; h < 4; ++h)
+                        if (wv[h] & kCodeClosed) lat.label[site + h] = tile_site(L, bx, by, rt[h]);
                 }
-                *reinterpret_cast<uint2 *>(lat.code + site) = codes;
+                uint8_t *eb = lat.edge + (size_t)tile * kEdgeBytes;
+                if (qx == 0 && c4 == 0) eb[TH + row2] = (uint8_t)(wv[0] & 0xFF);   // left edge: column 0
+                if (ext_right && c4 + 4 == ncols) eb[row2] = (uint8_t)(wv[3] & 0xFF);   // right edge: column tw - 1
             }
         }
         if (threadIdx.x == 0) lat.open_count[tile] = min(s_nopen, kOpenSlots);
@@ -934,21 +917,13 @@ __global__ void __launch_bounds__(kBlockThreads, 8) k_label_tiles(Batch b)
 }
 
 // ---------------------------------------------------------------------------
-// k_merge: union of the open roots across every active crossing bond.
+// k_merge: union of the open components across every active crossing bond.
 // Work items of a lattice: kMergeItems per tile, the 64 rows of its right
 // edge, then the 64 columns of its bottom edge; a warp takes 32
-// consecutive items (one side of one tile).
+// consecutive items (one side of one tile).  The slots of both ends come
+// from the edge bytes (right edge -> left edge of the next tile) or from
+// the codes of the bottom and top rows.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int open_root_of(const Lattice &lat, int site, int tile, bool &ok)
-{
-    const int code = lat.code[site];   // open site: slot of its root in the tile's open list
-    if (code & kCodeClosed) {
-        ok = false;
-        return site;
-    }
-    return __ldg(lat.open_list + (size_t)tile * kOpenSlots + code);
-}
-
 __global__ void k_merge(Batch b)
 {
     static_assert(kMergeItems == TH + TW, "merge items: right edge rows, then bottom edge columns");
@@ -962,7 +937,7 @@ __global__ void k_merge(Batch b)
          base += (long long)gridDim.x * blockDim.x) {
         const long long k = base + lane;
         bool ok = k < b.nmerge;
-        int a = 0, c2 = 0;
+        uint32_t a = 0, c2 = 0;
         if (ok) {
             if (k < lo || k >= hi) {
                 rep = find_rep(b.merge_off, b.nrep, k);
@@ -977,37 +952,38 @@ __global__ void k_merge(Batch b)
             const int X0 = bx * TW, Y0 = by * TH;
             const int tw = min(TW, L - X0), th = min(TH, L - Y0);
             const uint32_t *cw = lat.cross + (size_t)tile * kCrossWords;
-            int i, j, nt;
+            int sa = 0, sb = 0, nt;
             if (e < TH) {   // right edge, row e, into the next tile to the right
                 ok = e < th && ((__ldg(cw + (e >> 5)) >> (e & 31)) & 1u);
-                const int y = Y0 + e, x = X0 + tw - 1;
-                i = y * L + x;
-                j = y * L + (x + 1 == L ? 0 : x + 1);
                 nt = by * lat.tiles_x + (bx + 1 == lat.tiles_x ? 0 : bx + 1);
+                if (ok) {
+                    sa = lat.edge[(size_t)tile * kEdgeBytes + e];
+                    sb = lat.edge[(size_t)nt * kEdgeBytes + TH + e];
+                }
             } else {        // bottom edge, column e - 64, into the next tile below
                 const int c = e - TH;
                 ok = c < tw && ((__ldg(cw + 2 + (c >> 5)) >> (c & 31)) & 1u);
-                const int x = X0 + c, y = Y0 + th - 1;
-                i = y * L + x;
-                j = (y + 1 == L ? 0 : y + 1) * L + x;
-                nt = (by + 1 == lat.tiles_y ? 0 : by + 1) * lat.tiles_x + bx;
-            }
-            if (ok) {
-                bool open = true;
-                a = open_root_of(lat, i, tile, open);
-                c2 = open_root_of(lat, j, nt, open);
-                if (!open) {   // a crossing bond always ends at open sites
-                    record_error(lat.st, kErrInternal, i);
-                    ok = false;
+                const int yn = by + 1 == lat.tiles_y ? 0 : by + 1;
+                nt = yn * lat.tiles_x + bx;
+                if (ok) {
+                    sa = lat.code[(size_t)(Y0 + th - 1) * L + X0 + c];
+                    sb = lat.code[(size_t)yn * TH * L + X0 + c];
+                    if ((sa | sb) & kCodeClosed) {   // a crossing bond always ends at open sites
+                        record_error(lat.st, kErrInternal, (Y0 + th - 1) * L + X0 + c);
+                        ok = false;
+                    }
                 }
             }
+            a = (uint32_t)tile * kOpenSlots + (uint32_t)sa;
+            c2 = (uint32_t)nt * kOpenSlots + (uint32_t)sb;
         }
-        // Bonds of one warp that join the same two open roots need one union.
+        // Bonds of one warp that join the same two open components need one union.
         const unsigned vm = __ballot_sync(0xffffffffu, ok);
         if (ok) {
-            const unsigned long long key = ((unsigned long long)(unsigned)a << 32) | (unsigned)c2;
+            const unsigned long long key = ((unsigned long long)a << 32) | c2;
             const unsigned peers = __match_any_sync(vm, key);
-            if ((unsigned)__ffs(peers) - 1u == lane) union_roots(lat.label, a, c2, lat.L * lat.L + 1, lat.st);
+            if ((unsigned)__ffs(peers) - 1u == lane)
+                union_open(lat.opar, a, c2, lat.tiles_x * lat.tiles_y * kOpenSlots + 1, lat.st);
         }
     }
 }
@@ -1043,8 +1019,8 @@ __device__ void finish_sweep(const Batch &b)
 
 // ---------------------------------------------------------------------------
 // k_flip_tiles: the cluster roots and new states of the tile's open
-// components, all spin writes, state counts.  One block per tile, one warp
-// per quadrant.
+// components, all spin writes, state counts.  One block per tile; a thread
+// writes two 16-site chunks (chunk k: row k / 4, columns 16 (k % 4) ..).
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS, bool ANY_CLOCK>
 __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock : kFlipResidentPotts) k_flip_tiles(Batch b)
@@ -1058,9 +1034,8 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
-    const int warp = threadIdx.x >> 5, r = threadIdx.x & 31;
-    const int qx = warp & 1, qy = warp >> 1;
-    // q <= 8: state counts of this lane, 16 bits per state (states 0-3, 4-7);
+    const int r = threadIdx.x & 31;
+    // q <= 8: state counts of this thread, 16 bits per state (states 0-3, 4-7);
     // q == 2: sites in cnt_hi, sites in state 1 in cnt_lo.
     unsigned long long cnt_lo = 0, cnt_hi = 0;
     unsigned int open_roots = 0;   // clusters reaching a tile border, counted at their root
@@ -1112,83 +1087,114 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
         const int m = ctx.m;
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int X0 = bx * TW, Y0 = by * TH;
-        const int x0 = X0 + QW * qx, y0 = Y0 + QW * qy;                 // my quadrant
-        const int ncols = max(0, min(QW, min(TW, L - X0) - QW * qx));
-        const int nrows = max(0, min(QW, min(TH, L - Y0) - QW * qy));
-        // Lane -> 4 consecutive sites: columns cq..cq+3 of row 4 * step + rsub,
-        // so every warp access covers whole 32-byte sectors of 4 rows.
-        const int cq = (r & 7) * 4, rsub = r >> 3;
-        uint2 cw[8];
-        uint32_t sw[8];
+        const int tw = min(TW, L - X0), th = min(TH, L - Y0);
+        // My chunks: rows c0 / 4 and c0 / 4 + 32, columns 16 (c0 % 4) .. + 15.
+        const int crow = threadIdx.x >> 2, ccol = 16 * (threadIdx.x & 3);
+        const int cn = max(0, min(16, tw - ccol));   // valid columns of my chunks (a multiple of 4)
+        const bool vec = (L & 15) == 0;              // 16-byte aligned chunks
+        uint4 cwa[2], cwb[2], swv[2];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int row = 4 * k + rsub;
-            const bool v = row < nrows && cq < ncols;
-            const size_t site0 = (size_t)(y0 + row) * L + x0 + cq;
-            cw[k] = v ? *reinterpret_cast<const uint2 *>(lat.code + site0) : make_uint2(0u, 0u);
-            sw[k] = (clock && v) ? *reinterpret_cast<const uint32_t *>(lat.spin + site0) : 0u;
+        for (int j = 0; j < 2; ++j) {
+            const int rr = crow + 32 * j;
+            const bool v = rr < th && cn > 0;
+            const size_t site0 = (size_t)(Y0 + rr) * L + X0 + ccol;
+            cwa[j] = cwb[j] = swv[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (v) {
+                if (vec) {
+                    cwa[j] = *reinterpret_cast<const uint4 *>(lat.code + site0);
+                    cwb[j] = *reinterpret_cast<const uint4 *>(lat.code + site0 + 8);
+                    if (clock) swv[j] = *reinterpret_cast<const uint4 *>(lat.spin + site0);
+                } else {
+                    const uint2 *cp = reinterpret_cast<const uint2 *>(lat.code + site0);
+                    const uint32_t *sp = reinterpret_cast<const uint32_t *>(lat.spin + site0);
+                    uint32_t c8[8] = {0, 0, 0, 0, 0, 0, 0, 0}, s4[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+                        if (4 * g < cn) {
+                            const uint2 x = cp[g];
+                            c8[2 * g] = x.x;
+                            c8[2 * g + 1] = x.y;
+                            if (clock) s4[g] = sp[g];
+                        }
+                    cwa[j] = make_uint4(c8[0], c8[1], c8[2], c8[3]);
+                    cwb[j] = make_uint4(c8[4], c8[5], c8[6], c8[7]);
+                    swv[j] = make_uint4(s4[0], s4[1], s4[2], s4[3]);
+                }
+            }
         }
         // Every open component of the tile belongs to a cluster whose root
-        // (its smallest site, after the merge) draws the new state (Potts) or
-        // the reflection flag (clock), Sec. 2 (v)-(vii) / Sec. 4, into the
-        // tile's table.  A cluster is counted once, by the tile holding its root.
+        // (the component with the cluster's smallest site, after the merge)
+        // draws the new state (Potts) or the reflection flag (clock), Sec. 2
+        // (v)-(vii) / Sec. 4, into the tile's table.  A cluster is counted
+        // once, by the tile holding its root.
         {
-            const size_t k0 = (size_t)tile * kOpenSlots;
-            // Slot threadIdx.x is read before the count arrives (the list
-            // has kOpenSlots entries; those beyond the count are not used).
-            const int r0 = __ldg(lat.open_list + k0 + threadIdx.x);
             const int n = __ldg(lat.open_count + tile);
-            const int cap = L * L + 1;
+            const int cap = lat.tiles_x * lat.tiles_y * kOpenSlots + 1;
             for (int s = threadIdx.x; s < n; s += blockDim.x) {
-                const int r = s == (int)threadIdx.x ? r0 : __ldg(lat.open_list + k0 + s);
-                const int root = find_root_halving(lat.label, r, cap, lat.st);
-                if (MEASURE && root == r) ++open_roots;
-                const uint32_t u = draw4(lat, (uint32_t)root, ctx.t, kTagState).x;
+                const uint32_t x = (uint32_t)tile * kOpenSlots + (uint32_t)s;
+                const unsigned long long e = find_open(lat.opar, x, cap, lat.st);
+                const uint32_t key = (uint32_t)(e >> 32);
+                if (MEASURE && (uint32_t)e == x) ++open_roots;
+                const uint32_t u = draw4(lat, key, ctx.t, kTagState).x;
                 tab[s] = clock ? (unsigned char)(u >> 31) : (unsigned char)mulhi_q(u, q);
-                if (LABELS) rootg[LABELS ? s : 0] = root;
+                if (LABELS) rootg[LABELS ? s : 0] = (int)key;
             }
         }
         __syncthreads();
 
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int row = 4 * k + rsub;
-            if (!(row < nrows && cq < ncols)) continue;
-            const size_t site0 = (size_t)(y0 + row) * L + x0 + cq;
-            uint32_t word = 0;
+        for (int j = 0; j < 2; ++j) {
+            const int rr = crow + 32 * j;
+            if (!(rr < th && cn > 0)) continue;
+            const size_t site0 = (size_t)(Y0 + rr) * L + X0 + ccol;
+            const uint32_t cws[8] = {cwa[j].x, cwa[j].y, cwa[j].z, cwa[j].w, cwb[j].x, cwb[j].y, cwb[j].z, cwb[j].w};
+            const uint32_t sws[4] = {swv[j].x, swv[j].y, swv[j].z, swv[j].w};
+            uint32_t out[4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const uint32_t code = ((h < 2) ? (cw[k].x >> (16 * h)) : (cw[k].y >> (16 * (h - 2)))) & 0xFFFFu;
-                int ns;
-                if (clock) {   // closed: the cluster's flag in the code; open: its root's, in the table
-                    const int k0 = valid_state((int)((sw[k] >> (8 * h)) & 0xFFu), q);
-                    ns = ((code & kCodeClosed) ? (code & 1u) : tab[code & 0xFFu]) ? reflect(k0, m, q) : k0;
-                } else {
-                    ns = tab[min(code, (uint32_t)(kOpenSlots + SW_MAX_Q - 1))];   // open slot or kCodeClosed | state
+            for (int g = 0; g < 4; ++g) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const uint32_t code = (cws[2 * g + (h >> 1)] >> (16 * (h & 1))) & 0xFFFFu;
+                    int ns;
+                    if (clock) {   // closed: the cluster's flag in the code; open: its root's, in the table
+                        const int k0 = valid_state((int)((sws[g] >> (8 * h)) & 0xFFu), q);
+                        ns = ((code & kCodeClosed) ? (code & 1u) : tab[code & 0xFFu]) ? reflect(k0, m, q) : k0;
+                    } else {
+                        ns = tab[min(code, (uint32_t)(kOpenSlots + SW_MAX_Q - 1))];   // open slot or kCodeClosed | state
+                    }
+                    if (MEASURE && q > 2 && q <= 8 && 4 * g < cn) {
+                        const unsigned long long one = 1ull << (16 * (ns & 3));
+                        if (ns < 4) cnt_lo += one;
+                        else cnt_hi += one;
+                    }
+                    if (LABELS && 4 * g < cn && !(code & kCodeClosed))
+                        lat.label[site0 + 4 * g + h] = rootg[LABELS ? (code & 0xFF) : 0];
+                    word |= (uint32_t)(ns & 0xFF) << (8 * h);
                 }
-                if (MEASURE && q > 2 && q <= 8) {
-                    const unsigned long long one = 1ull << (16 * (ns & 3));
-                    if (ns < 4) cnt_lo += one;
-                    else cnt_hi += one;
+                out[g] = word;
+                if (MEASURE && q == 2 && 4 * g < cn) {   // states are 0 or 1
+                    cnt_lo += (unsigned)__popc(word);
+                    cnt_hi += 4u;
                 }
-                if (LABELS && !(code & kCodeClosed))
-                    lat.label[site0 + h] = rootg[LABELS ? code : 0];
-                word |= (uint32_t)(ns & 0xFF) << (8 * h);
             }
-            if (MEASURE && q == 2) {   // states are 0 or 1
-                cnt_lo += (unsigned)__popc(word);
-                cnt_hi += 4u;
+            if (vec) {
+                *reinterpret_cast<uint4 *>(lat.spin + site0) = make_uint4(out[0], out[1], out[2], out[3]);
+            } else {
+                uint32_t *sp = reinterpret_cast<uint32_t *>(lat.spin + site0);
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    if (4 * g < cn) sp[g] = out[g];
             }
-            *reinterpret_cast<uint32_t *>(lat.spin + site0) = word;
         }
         if (MEASURE && q > 8) {
             // Many states: warp-aggregated shared histogram, site by site.
 #pragma unroll 1
-            for (int k = 0; k < 8; ++k) {
-                const int row = 4 * k + rsub;
-                const bool v = row < nrows && cq < ncols;
-                const size_t site0 = (size_t)(y0 + row) * L + x0 + cq;
-                for (int h = 0; h < 4; ++h) {
+            for (int j = 0; j < 2; ++j) {
+                const int rr = crow + 32 * j;
+                const size_t site0 = (size_t)(Y0 + rr) * L + X0 + ccol;
+                for (int h = 0; h < 16; ++h) {
+                    const bool v = rr < th && h < cn;
                     const int ns = v ? (int)lat.spin[site0 + h] : 0;
                     add_hist_any(hist_state, ns, v && ns >= 0 && ns < q);
                 }
