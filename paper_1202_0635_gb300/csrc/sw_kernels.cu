@@ -924,12 +924,12 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
 // from the edge bytes (right edge -> left edge of the next tile) or from
 // the codes of the bottom and top rows.
 // ---------------------------------------------------------------------------
-__global__ void k_merge(Batch b)
+__global__ void __launch_bounds__(256, 8) k_merge(Batch b)
 {
     static_assert(kMergeItems == TH + TW, "merge items: right edge rows, then bottom edge columns");
     long long lo = 0, hi = 0;
     int rep = -1;
-    Lattice lat;
+    const Lattice *lp = b.lat;   // read through the L1, not copied into registers
     const unsigned lane = threadIdx.x & 31;
     // Every lattice has a multiple of kMergeItems items: a warp never spans
     // two lattices, and its trip count is uniform.
@@ -943,8 +943,9 @@ __global__ void k_merge(Batch b)
                 rep = find_rep(b.merge_off, b.nrep, k);
                 lo = __ldg(b.merge_off + rep);
                 hi = __ldg(b.merge_off + rep + 1);
-                lat = b.lat[rep];
+                lp = b.lat + rep;
             }
+            const Lattice &lat = *lp;
             const int L = lat.L;
             const int kk = (int)(k - lo);
             const int tile = kk / kMergeItems, e = kk % kMergeItems;
@@ -983,7 +984,7 @@ __global__ void k_merge(Batch b)
             const unsigned long long key = ((unsigned long long)a << 32) | c2;
             const unsigned peers = __match_any_sync(vm, key);
             if ((unsigned)__ffs(peers) - 1u == lane)
-                union_open(lat.opar, a, c2, lat.tiles_x * lat.tiles_y * kOpenSlots + 1, lat.st);
+                union_open(lp->opar, a, c2, lp->tiles_x * lp->tiles_y * kOpenSlots + 1, lp->st);
         }
     }
 }
