@@ -206,6 +206,17 @@ int sw_set_labeling(sw_handle *h, int method);
 /* Scan passes of the last comparator sweep (0 for the tiled labeling). */
 int sw_label_passes(sw_handle *h);
 
+/* Test aid, not needed for simulation.  loop_cap > 0: every data-dependent
+ * device loop of the sweep (union-find walks and links in shared and global
+ * memory) gives up after loop_cap steps and records a device error, which
+ * the next sw_sweep / sw_measure / sw_synchronize reports as the sticky
+ * SW_ERR_NOT_CONVERGED (results of that sweep are undefined); no loop can
+ * run longer than its cap.  list_cap > 0: a tile's list of union pairs holds
+ * at most list_cap pairs; the rest are joined by the threads that found
+ * them (same results, the path taken when the list overflows).  0 restores
+ * the default of either.  Negative values: SW_ERR_ARG. */
+int sw_set_debug_limits(sw_handle *h, int loop_cap, int list_cap);
+
 /* Use a different stream for subsequent work (a cudaStream_t). */
 int sw_set_stream(sw_handle *h, void *stream);
 

@@ -88,6 +88,7 @@ EXPORTS = [
     ("sw_profile_sweeps", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     ("sw_autotune", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("sw_set_launch_shape", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
+    ("sw_set_debug_limits", ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
     ("sw_batch_create", ctypes.c_void_p, [ctypes.c_void_p]),
     ("sw_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("sw_batch_attach", ctypes.c_int, [ctypes.c_void_p, _H]),
@@ -326,6 +327,10 @@ def sw_batch_profile_sweeps(b, n):
     out = np.zeros(8, dtype=np.float32)
     m = _check(lib().sw_batch_profile_sweeps(b, int(n), _p(out, ctypes.c_float), 8))
     return [float(v) for v in out[:m]]
+
+
+def sw_set_debug_limits(h, loop_cap, list_cap):
+    return _check(lib().sw_set_debug_limits(h, int(loop_cap), int(list_cap)))
 
 
 def sw_set_labeling(h, method):

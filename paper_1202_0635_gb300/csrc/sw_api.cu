@@ -107,6 +107,7 @@ struct sw_handle {
     uint32_t thr = 0;
     std::vector<uint32_t> thr_tab;
     int ncounters = 0, nclass = 0;
+    int dbg_loop_cap = 0, dbg_list_cap = 0;   // test aids (sw_set_debug_limits)
     bool measure = true, labels = false, record = false, use_graph = false;
     LaunchShape shape;
     uint64_t t_host = 0;       // sweep index after all enqueued work
@@ -148,6 +149,8 @@ struct sw_handle {
         lat.ring_slots = swgb::kRingSlots;
         lat.ncounters = ncounters;
         lat.nclass = nclass;
+        lat.dbg_loop_cap = dbg_loop_cap;
+        lat.dbg_list_cap = dbg_list_cap;
         return lat;
     }
 
@@ -1033,6 +1036,21 @@ int sw_label_passes(sw_handle *h)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
     return h->last_passes;
+}
+
+int sw_set_debug_limits(sw_handle *h, int loop_cap, int list_cap)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    if (loop_cap < 0 || list_cap < 0) return fail(SW_ERR_ARG, "limits must be >= 0 (0: default)");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    h->dbg_loop_cap = loop_cap;
+    h->dbg_list_cap = list_cap;
+    const Lattice self = h->lattice();
+    SW_CUDA(cudaMemcpyAsync(h->d_self, &self, sizeof self, cudaMemcpyHostToDevice, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->owner) h->owner->dirty = true;
+    return SW_OK;
 }
 
 int sw_set_graph(sw_handle *h, int on)

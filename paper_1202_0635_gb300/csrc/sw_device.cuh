@@ -53,6 +53,11 @@ struct Lattice {
     int ring_slots;
     int ncounters;
     int nclass;
+    // Test aids (0: defaults): every data-dependent device loop gives up
+    // after dbg_loop_cap steps (recording kErrFindCap / kErrUnionCap), and a
+    // tile's union-pair list holds at most dbg_list_cap pairs.
+    int dbg_loop_cap;
+    int dbg_list_cap;
 };
 
 // A set of lattices swept together; a single lattice is a batch of one.

@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
     // The union pairs (provisional labels of both ends, packed in a word);
     // then the list of provisional labels.
     __shared__ __align__(16) uint16_t rlist[NS];
-    uint32_t *ulist = reinterpret_cast<uint32_t *>(rlist);
+    uint32_t *upairs = reinterpret_cast<uint32_t *>(rlist);
     constexpr int kUnionList = NS / 2;
     __shared__ __align__(16) RowMasks sm[TH][2];      // scan masks by (row, half)
     __shared__ unsigned int openw[NS / 32];           // open roots
@@ -669,6 +669,8 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
         const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
         const bool ext_right = QW * qx + ncols == tw;                   // my right edge is the tile's
         const bool ext_bottom = QW * qy + nrows == th;
+        const int cap = lat.dbg_loop_cap > 0 ? lat.dbg_loop_cap : NS + 1;   // loop bound
+        const int ulist = lat.dbg_list_cap > 0 ? min(kUnionList, lat.dbg_list_cap) : kUnionList;
 
         // ===== masks (lane = row; bond masks written by k_bonds) ================
         unsigned S = 0u, U2 = 0u;
@@ -756,9 +758,9 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
             auto put = [&](int a, int bn) {
                 const uint32_t la = (uint32_t)X[a], lb = (uint32_t)X[bn];
                 const uint32_t pr = la == lb ? 0u : (la | (lb << 16));
-                if (at < kUnionList) {
-                    ulist[at] = pr;
-                } else if (!union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), NS + 1)) {
+                if (at < ulist) {
+                    upairs[at] = pr;
+                } else if (!union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), cap)) {
                     record_error(lat.st, kErrUnionCap, Y0 * L + X0);
                 }
                 ++at;
@@ -773,13 +775,13 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
         }
         __syncthreads();
         {
-            const int np = min(s_npairs, kUnionList);
+            const int np = min(s_npairs, ulist);
             for (int i0 = 0; i0 < np; i0 += blockDim.x) {   // uniform trip count: warp-wide dedup
                 const int i = i0 + threadIdx.x;
-                const uint32_t pr = i < np ? ulist[i] : 0u;
+                const uint32_t pr = i < np ? upairs[i] : 0u;
                 const unsigned peers = __match_any_sync(FULL, pr);
                 if (pr != 0u && (__ffs(peers) - 1) == lane &&
-                    !union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), NS + 1))
+                    !union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), cap))
                     record_error(lat.st, kErrUnionCap, Y0 * L + X0);
             }
         }
@@ -802,7 +804,7 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
             }
             int rt = -1;
             if (node >= 0) {
-                rt = find_t_ro(X, X[node], NS + 1);
+                rt = find_t_ro(X, X[node], cap);
                 if (rt < 0) record_error(lat.st, kErrFindCap, Y0 * L + X0);
             }
             const unsigned peers = __match_any_sync(FULL, rt);   // one atomic per distinct root
@@ -833,11 +835,16 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
             for (int i = threadIdx.x; i < nlab; i += blockDim.x) {
                 const int v = rlist[i];
                 int x = v;
-                for (int it = 0; it <= NS; ++it) {   // read-only: stops at a root, settled or not
+                bool found = false;
+                for (int it = 0; it < cap; ++it) {   // read-only: stops at a root, settled or not
                     const int p = X[x];
-                    if (p == x || p >= kTileResolved) break;
+                    if (p == x || p >= kTileResolved) {
+                        found = true;
+                        break;
+                    }
                     x = p;
                 }
+                if (!found) record_error(lat.st, kErrFindCap, Y0 * L + X0);
                 if (x != v) {
                     X[v] = (uint16_t)x;
                     continue;
@@ -984,7 +991,8 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
             const unsigned long long key = ((unsigned long long)a << 32) | c2;
             const unsigned peers = __match_any_sync(vm, key);
             if ((unsigned)__ffs(peers) - 1u == lane)
-                union_open(lp->opar, a, c2, lp->tiles_x * lp->tiles_y * kOpenSlots + 1, lp->st);
+                union_open(lp->opar, a, c2,
+                           lp->dbg_loop_cap > 0 ? lp->dbg_loop_cap : lp->tiles_x * lp->tiles_y * kOpenSlots + 1, lp->st);
         }
     }
 }
@@ -1130,7 +1138,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
         // once, by the tile holding its root.
         {
             const int n = __ldg(lat.open_count + tile);
-            const int cap = lat.tiles_x * lat.tiles_y * kOpenSlots + 1;
+            const int cap = lat.dbg_loop_cap > 0 ? lat.dbg_loop_cap : lat.tiles_x * lat.tiles_y * kOpenSlots + 1;
             for (int s = threadIdx.x; s < n; s += blockDim.x) {
                 const uint32_t x = (uint32_t)tile * kOpenSlots + (uint32_t)s;
                 const unsigned long long e = find_open(lat.opar, x, cap, lat.st);
