@@ -217,6 +217,29 @@ int sw_label_passes(sw_handle *h);
  * the default of either.  Negative values: SW_ERR_ARG. */
 int sw_set_debug_limits(sw_handle *h, int loop_cap, int list_cap);
 
+/* Labeling statistics, the counterpart of the paper's labeling-iteration
+ * count (Sec. 4: the passes a whole-lattice labeling needs grow near and
+ * below T_c).  on = 1 starts (and zeroes) per-lattice device tallies of the
+ * following sweeps, 0 stops and frees them; while on, the merge and flip
+ * kernels run variants that tally (slower).  sw_get_labeling_stats writes
+ * up to n of these values (per sweep, per tile where stated) and returns
+ * how many it wrote:
+ *   0 sweeps tallied
+ *   1 provisional labels opened by the tile scans, per tile
+ *   2 union pairs of the tiles (further run contacts, quadrant seams), per tile
+ *   3 tile components (clusters inside a tile + open components), per tile
+ *   4 open components (reaching a tile border), per tile
+ *   5 unions across tile edges (distinct component pairs), per sweep
+ *   6 link attempts per union (atomicMin on a root entry)
+ *   7 attempts that found the root linked meanwhile, per attempt
+ *   8 walks of the global union-find (merge and root walks), per sweep
+ *   9 parent steps per walk
+ *   10 the longest walk (steps)
+ * Values 1-4 are exact functions of the bonds; 5-10 depend on the order in
+ * which the GPU's threads meet.  SW_ERR_STATE if the statistics are off. */
+int sw_set_labeling_stats(sw_handle *h, int on);
+int sw_get_labeling_stats(sw_handle *h, double *out, int n);
+
 /* Use a different stream for subsequent work (a cudaStream_t). */
 int sw_set_stream(sw_handle *h, void *stream);
 

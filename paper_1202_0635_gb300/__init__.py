@@ -89,6 +89,8 @@ EXPORTS = [
     ("sw_autotune", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("sw_set_launch_shape", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     ("sw_set_debug_limits", ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    ("sw_set_labeling_stats", ctypes.c_int, [_H, ctypes.c_int]),
+    ("sw_get_labeling_stats", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("sw_batch_create", ctypes.c_void_p, [ctypes.c_void_p]),
     ("sw_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("sw_batch_attach", ctypes.c_int, [ctypes.c_void_p, _H]),
@@ -331,6 +333,22 @@ def sw_batch_profile_sweeps(b, n):
 
 def sw_set_debug_limits(h, loop_cap, list_cap):
     return _check(lib().sw_set_debug_limits(h, int(loop_cap), int(list_cap)))
+
+
+LABELING_STATS = ("sweeps", "labels_per_tile", "pairs_per_tile", "components_per_tile", "open_per_tile",
+                  "unions_per_sweep", "links_per_union", "retries_per_link", "walks_per_sweep", "steps_per_walk",
+                  "max_steps")
+
+
+def sw_set_labeling_stats(h, on):
+    return _check(lib().sw_set_labeling_stats(h, int(on)))
+
+
+def sw_get_labeling_stats(h):
+    """The labeling statistics as a dict (names in LABELING_STATS)."""
+    out = np.zeros(len(LABELING_STATS), dtype=np.float64)
+    m = _check(lib().sw_get_labeling_stats(h, _p(out, ctypes.c_double), len(out)))
+    return {k: float(out[i]) for i, k in enumerate(LABELING_STATS[:m])}
 
 
 def sw_set_labeling(h, method):

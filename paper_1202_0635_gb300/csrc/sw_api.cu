@@ -82,6 +82,7 @@ struct sw_handle {
     unsigned long long *d_opar = nullptr;
     uint8_t *d_edge = nullptr;
     int32_t *d_open_count = nullptr;
+    unsigned long long *d_stats = nullptr;   // labeling statistics (sw_set_labeling_stats)
     uint32_t *d_cross = nullptr;
     uint32_t *d_bond = nullptr;
     int tiles_x = 0, tiles_y = 0;
@@ -151,6 +152,7 @@ struct sw_handle {
         lat.nclass = nclass;
         lat.dbg_loop_cap = dbg_loop_cap;
         lat.dbg_list_cap = dbg_list_cap;
+        lat.stats = d_stats;
         return lat;
     }
 
@@ -169,6 +171,7 @@ struct sw_handle {
         b.ntasks = ntasks();
         b.nmerge = nmerge();
         b.any_clock = model == SW_CLOCK;
+        b.any_stats = d_stats != nullptr;
         return b;
     }
 };
@@ -190,7 +193,7 @@ struct sw_batch {
     unsigned int *d_ticket = nullptr;
     int ntasks = 0;
     long long nmerge = 0;
-    bool any_clock = false;
+    bool any_clock = false, any_stats = false;
     int nrep = 0;                 // lattices in the descriptor arrays
     bool dirty = true;
     cudaGraph_t graph = nullptr;
@@ -207,6 +210,7 @@ struct sw_batch {
         b.ntasks = ntasks;
         b.nmerge = nmerge;
         b.any_clock = any_clock;
+        b.any_stats = any_stats;
         return b;
     }
 };
@@ -538,6 +542,7 @@ void free_handle(sw_handle *h)
     if (h->d_bond) cudaFree(h->d_bond);
     if (h->d_st) cudaFree(h->d_st);
     if (h->d_ring) cudaFree(h->d_ring);
+    if (h->d_stats) cudaFree(h->d_stats);
     if (h->d_self) cudaFree(h->d_self);
     if (h->d_task_off) cudaFree(h->d_task_off);
     if (h->d_merge_off) cudaFree(h->d_merge_off);
@@ -1053,6 +1058,56 @@ int sw_set_debug_limits(sw_handle *h, int loop_cap, int list_cap)
     return SW_OK;
 }
 
+int sw_set_labeling_stats(sw_handle *h, int on)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    if (on && !h->d_stats) SW_CUDA(cudaMalloc(&h->d_stats, sizeof(unsigned long long) * swgb::kStatFields));
+    if (!on && h->d_stats) {
+        cudaFree(h->d_stats);
+        h->d_stats = nullptr;
+    }
+    if (h->d_stats)
+        SW_CUDA(cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * swgb::kStatFields, h->stream));
+    const Lattice self = h->lattice();
+    SW_CUDA(cudaMemcpyAsync(h->d_self, &self, sizeof self, cudaMemcpyHostToDevice, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    drop_graph(h);   // the kernel variants depend on it
+    if (h->owner) h->owner->dirty = true;
+    return SW_OK;
+}
+
+int sw_get_labeling_stats(sw_handle *h, double *out, int n)
+{
+    if (!h || !out) return fail(SW_ERR_ARG, "null argument");
+    if (!h->d_stats) return fail(SW_ERR_STATE, "labeling statistics are off (sw_set_labeling_stats)");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    unsigned long long a[swgb::kStatFields];
+    SW_CUDA(cudaMemcpyAsync(a, h->d_stats, sizeof a, cudaMemcpyDeviceToHost, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    const double sweeps = (double)a[swgb::kStatSweeps];
+    const double ts = sweeps * (double)h->ntiles();
+    auto ratio = [](double x, double y) { return y > 0.0 ? x / y : 0.0; };
+    const double v[11] = {
+        sweeps,
+        ratio((double)a[swgb::kStatLabels], ts),
+        ratio((double)a[swgb::kStatPairs], ts),
+        ratio((double)a[swgb::kStatComponents], ts),
+        ratio((double)a[swgb::kStatOpen], ts),
+        ratio((double)a[swgb::kStatUnions], sweeps),
+        ratio((double)a[swgb::kStatLinks], (double)a[swgb::kStatUnions]),
+        ratio((double)a[swgb::kStatRetries], (double)a[swgb::kStatLinks]),
+        ratio((double)a[swgb::kStatFinds], sweeps),
+        ratio((double)a[swgb::kStatHops], (double)a[swgb::kStatFinds]),
+        (double)a[swgb::kStatMaxHops],
+    };
+    const int m = std::min(n, 11);
+    for (int i = 0; i < m; ++i) out[i] = v[i];
+    return m;
+}
+
 int sw_set_graph(sw_handle *h, int on)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
@@ -1104,11 +1159,16 @@ static int rebuild_batch(sw_batch *b)
         task_off[i + 1] = task_off[i] + b->reps[i]->ntasks();
         merge_off[i + 1] = merge_off[i] + b->reps[i]->nmerge();
     }
-    bool any_clock = false;
-    for (int i = 0; i < n; ++i) any_clock = any_clock || b->reps[i]->model == SW_CLOCK;
+    bool any_clock = false, any_stats = false;
+    for (int i = 0; i < n; ++i) {
+        any_clock = any_clock || b->reps[i]->model == SW_CLOCK;
+        any_stats = any_stats || b->reps[i]->d_stats != nullptr;
+    }
     // A captured graph holds the kernel parameters of the batch view.
-    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge || any_clock != b->any_clock || n != b->nrep)
+    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge || any_clock != b->any_clock ||
+        any_stats != b->any_stats || n != b->nrep)
         drop_batch_graph(b);
+    b->any_stats = any_stats;
     b->ntasks = task_off[n];
     b->nmerge = merge_off[n];
     b->any_clock = any_clock;

@@ -58,6 +58,25 @@ struct Lattice {
     // tile's union-pair list holds at most dbg_list_cap pairs.
     int dbg_loop_cap;
     int dbg_list_cap;
+    // Labeling statistics (nullptr: not gathered): kStat* accumulators.
+    unsigned long long *stats;
+};
+
+// Accumulators of the labeling statistics, summed over the sweeps that ran
+// with them on.
+enum : int {
+    kStatLabels = 0,      // provisional labels opened by the tile scans
+    kStatPairs = 1,       // union pairs of the tiles (further run contacts and quadrant seams)
+    kStatComponents = 2,  // tile components (closed clusters and open components)
+    kStatOpen = 3,        // open components (reaching a tile border)
+    kStatUnions = 4,      // global unions across tile edges (distinct component pairs of a warp)
+    kStatLinks = 5,       // global link attempts (atomicMin of a root entry)
+    kStatRetries = 6,     // link attempts that found the root linked meanwhile
+    kStatFinds = 7,       // global walks (merge and root walks)
+    kStatHops = 8,        // parent steps of those walks
+    kStatMaxHops = 9,     // longest walk (steps)
+    kStatSweeps = 10,     // sweeps counted
+    kStatFields = 11
 };
 
 // A set of lattices swept together; a single lattice is a batch of one.
@@ -72,6 +91,7 @@ struct Batch {
     int ntasks;
     long long nmerge;
     int any_clock;                 // a clock lattice is present (selects the kernel variant that measures it)
+    int any_stats;                 // a lattice gathers labeling statistics (selects the variants that tally)
 };
 
 // Philox-4x32-10 (Salmon et al., SC'11).  Each round takes two 32x32->64
@@ -134,17 +154,35 @@ __device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long 
     return *reinterpret_cast<const volatile unsigned long long *>(p);
 }
 
-// Root entry of node x (key << 32 | root id).
-__device__ __forceinline__ unsigned long long find_open(unsigned long long *par, uint32_t x, int cap, DevState *st)
+// Tallies of the global union-find (labeling statistics).
+struct OpenTally {
+    unsigned int finds = 0, hops = 0, max_hops = 0, links = 0, retries = 0;
+};
+
+// Root entry of node x (key << 32 | root id).  Parent steps go to the tally.
+__device__ __forceinline__ unsigned long long find_open(unsigned long long *par, uint32_t x, int cap, DevState *st,
+                                                        OpenTally &tl)
 {
     const long long t0 = clock64();
+    ++tl.finds;
+    unsigned int steps = 0;
     for (int it = 0; it < cap; ++it) {
         const unsigned long long e = ld_volatile64(par + x);
         const uint32_t p = (uint32_t)e;
-        if (p == x) return e;
+        if (p == x) {
+            tl.hops += steps;
+            tl.max_hops = max(tl.max_hops, steps);
+            return e;
+        }
         const unsigned long long ep = ld_volatile64(par + p);
         const uint32_t gp = (uint32_t)ep;
-        if (gp == p) return ep;
+        ++steps;
+        if (gp == p) {
+            tl.hops += steps;
+            tl.max_hops = max(tl.max_hops, steps);
+            return ep;
+        }
+        ++steps;
         par[x] = ep;   // grandparent: an ancestor of x, safe under concurrent linking
         x = gp;
         if ((it & 255) == 255 && clock64() - t0 > kLoopBudgetCycles) {
@@ -156,22 +194,25 @@ __device__ __forceinline__ unsigned long long find_open(unsigned long long *par,
     return ld_volatile64(par + x);
 }
 
-__device__ __forceinline__ void union_open(unsigned long long *par, uint32_t a, uint32_t b, int cap, DevState *st)
+__device__ __forceinline__ void union_open(unsigned long long *par, uint32_t a, uint32_t b, int cap, DevState *st,
+                                           OpenTally &tl)
 {
     const long long t0 = clock64();
     // Both entries in flight at once: most ends are roots already.
     unsigned long long ea = ld_volatile64(par + a), eb = ld_volatile64(par + b);
-    if ((uint32_t)ea != a) ea = find_open(par, a, cap, st);
-    if ((uint32_t)eb != b) eb = find_open(par, b, cap, st);
+    if ((uint32_t)ea != a) ea = find_open(par, a, cap, st, tl);
+    if ((uint32_t)eb != b) eb = find_open(par, b, cap, st, tl);
     for (int it = 0; it < cap; ++it) {
         if (ea == eb) return;
         const unsigned long long hi = ea > eb ? ea : eb;
         const unsigned long long lo = ea > eb ? eb : ea;
         const unsigned long long old = atomicMin(par + (uint32_t)hi, lo);
+        ++tl.links;
         if (old == hi) return;   // hi was a root: now under lo
+        ++tl.retries;
         // hi had been linked under old meanwhile: join old's tree and lo's.
-        ea = find_open(par, (uint32_t)old, cap, st);
-        eb = find_open(par, (uint32_t)lo, cap, st);
+        ea = find_open(par, (uint32_t)old, cap, st, tl);
+        eb = find_open(par, (uint32_t)lo, cap, st, tl);
         if (clock64() - t0 > kLoopBudgetCycles) {
             record_error(st, kErrTimeBudget, (int)(uint32_t)hi);
             return;
@@ -257,6 +298,23 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, unsigned int 
         if (lane == 0 && s) atomicAdd(dst, (unsigned long long)s);
     }
     __syncthreads();
+}
+
+// Block-wide flush of the global union-find tallies into a lattice's
+// statistics (all threads of the block; no-op without statistics).  unions:
+// the thread's unions attempted.
+template <int NT>
+__device__ __forceinline__ void flush_open_tally(unsigned long long *stats, const OpenTally &tl, unsigned int unions,
+                                                 unsigned int *scratch)
+{
+    if (stats == nullptr) return;   // uniform: one lattice per block call
+    block_add<NT>(stats + kStatUnions, unions, scratch);
+    block_add<NT>(stats + kStatLinks, tl.links, scratch);
+    block_add<NT>(stats + kStatRetries, tl.retries, scratch);
+    block_add<NT>(stats + kStatFinds, tl.finds, scratch);
+    block_add<NT>(stats + kStatHops, tl.hops, scratch);
+    const unsigned int m = __reduce_max_sync(0xffffffffu, tl.max_hops);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(stats + kStatMaxHops, (unsigned long long)m);
 }
 
 }  // namespace swgb

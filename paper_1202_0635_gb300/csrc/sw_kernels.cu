@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
     constexpr int kUnionList = NS / 2;
     __shared__ __align__(16) RowMasks sm[TH][2];      // scan masks by (row, half)
     __shared__ unsigned int openw[NS / 32];           // open roots
-    __shared__ int s_nroots, s_nopen, s_npairs;
+    __shared__ int s_nroots, s_nopen, s_npairs, s_nclosed;
     __shared__ unsigned int s_cross[kCrossWords];
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
         }
         openw[threadIdx.x] = 0u;
         static_assert(NS / 32 == kBlockThreads, "one open word per thread");
-        if (threadIdx.x == 0) s_nroots = s_nopen = s_npairs = 0;
+        if (threadIdx.x == 0) s_nroots = s_nopen = s_npairs = s_nclosed = 0;
         __syncthreads();
 
         // ===== scan (lane = column): provisional labels row by row ============
@@ -865,6 +865,7 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
                     const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
                     w = kTileResolved | kCodeClosed | (clock ? (int)(u >> 31) : mulhi_q(u, q));
                     ++closed_roots;
+                    if (lat.stats) atomicAdd(&s_nclosed, 1);
                 }
                 X[v] = (uint16_t)w;
             }
@@ -912,7 +913,15 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
                 if (ext_right && c4 + 4 == ncols) eb[row2] = (uint8_t)(wv[3] & 0xFF);   // right edge: column tw - 1
             }
         }
-        if (threadIdx.x == 0) lat.open_count[tile] = min(s_nopen, kOpenSlots);
+        if (threadIdx.x == 0) {
+            lat.open_count[tile] = min(s_nopen, kOpenSlots);
+            if (lat.stats) {   // labeling statistics of the tile
+                atomicAdd(lat.stats + kStatLabels, (unsigned long long)s_nroots);
+                atomicAdd(lat.stats + kStatPairs, (unsigned long long)s_npairs);
+                atomicAdd(lat.stats + kStatComponents, (unsigned long long)(s_nopen + s_nclosed));
+                atomicAdd(lat.stats + kStatOpen, (unsigned long long)s_nopen);
+            }
+        }
         if (threadIdx.x < kCrossWords) {
             // Zeroed by its only reader, ready for the next task.
             lat.cross[(size_t)tile * kCrossWords + threadIdx.x] = s_cross[threadIdx.x];
@@ -931,6 +940,9 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
 // from the edge bytes (right edge -> left edge of the next tile) or from
 // the codes of the bottom and top rows.
 // ---------------------------------------------------------------------------
+// STATS: a lattice of the batch gathers labeling statistics (the walk tallies
+// are compiled in).
+template <bool STATS>
 __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
 {
     static_assert(kMergeItems == TH + TW, "merge items: right edge rows, then bottom edge columns");
@@ -938,6 +950,26 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
     int rep = -1;
     const Lattice *lp = b.lat;   // read through the L1, not copied into registers
     const unsigned lane = threadIdx.x & 31;
+    OpenTally tl;           // labeling statistics of the warp's current lattice
+    unsigned int unions = 0;
+    // A warp's items all belong to one lattice at a time: its tallies go to
+    // that lattice's statistics (warp sums) when it moves on or finishes.
+    auto flush_warp = [&]() {
+        unsigned long long *st = lp->stats;
+        if (st != nullptr) {
+            const unsigned v[6] = {unions, tl.links, tl.retries, tl.finds, tl.hops, 0u};
+            const int f[5] = {kStatUnions, kStatLinks, kStatRetries, kStatFinds, kStatHops};
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const unsigned s = __reduce_add_sync(0xffffffffu, v[i]);
+                if (lane == 0 && s) atomicAdd(st + f[i], (unsigned long long)s);
+            }
+            const unsigned m = __reduce_max_sync(0xffffffffu, tl.max_hops);
+            if (lane == 0 && m) atomicMax(st + kStatMaxHops, (unsigned long long)m);
+        }
+        tl = OpenTally();
+        unions = 0;
+    };
     // Every lattice has a multiple of kMergeItems items: a warp never spans
     // two lattices, and its trip count is uniform.
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < b.nmerge;
@@ -947,6 +979,7 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
         uint32_t a = 0, c2 = 0;
         if (ok) {
             if (k < lo || k >= hi) {
+                if (STATS && rep >= 0) flush_warp();   // uniform: the warp's items share a lattice
                 rep = find_rep(b.merge_off, b.nrep, k);
                 lo = __ldg(b.merge_off + rep);
                 hi = __ldg(b.merge_off + rep + 1);
@@ -990,11 +1023,15 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
         if (ok) {
             const unsigned long long key = ((unsigned long long)a << 32) | c2;
             const unsigned peers = __match_any_sync(vm, key);
-            if ((unsigned)__ffs(peers) - 1u == lane)
+            if ((unsigned)__ffs(peers) - 1u == lane) {
+                ++unions;
                 union_open(lp->opar, a, c2,
-                           lp->dbg_loop_cap > 0 ? lp->dbg_loop_cap : lp->tiles_x * lp->tiles_y * kOpenSlots + 1, lp->st);
+                           lp->dbg_loop_cap > 0 ? lp->dbg_loop_cap : lp->tiles_x * lp->tiles_y * kOpenSlots + 1, lp->st,
+                           tl);
+            }
         }
     }
+    if (STATS && rep >= 0) flush_warp();
 }
 
 // Last block of the sweep's final kernel: for every lattice of the batch,
@@ -1019,6 +1056,7 @@ __device__ void finish_sweep(const Batch &b)
         const bool counted = MEASURE && t >= 1ull && t - 1ull >= read_u64(&lt.st->classes_upto);
         unsigned long long *next = ring_row(lt, t + 1);
         for (int c = 0; c < lt.ncounters; ++c) next[c] = 0ull;
+        if (lt.stats) lt.stats[kStatSweeps] += 1ull;
         if (counted) lt.st->classes_upto = t;
         __threadfence();
         *reinterpret_cast<volatile unsigned long long *>(&lt.st->sweep) = t + 1;
@@ -1031,7 +1069,7 @@ __device__ void finish_sweep(const Batch &b)
 // components, all spin writes, state counts.  One block per tile; a thread
 // writes two 16-site chunks (chunk k: row k / 4, columns 16 (k % 4) ..).
 // ---------------------------------------------------------------------------
-template <bool MEASURE, bool LABELS, bool ANY_CLOCK>
+template <bool MEASURE, bool LABELS, bool ANY_CLOCK, bool STATS>
 __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock : kFlipResidentPotts) k_flip_tiles(Batch b)
 {
     // New state (Potts) or reflection flag (clock) of each open slot; then
@@ -1048,10 +1086,13 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
     // q == 2: sites in cnt_hi, sites in state 1 in cnt_lo.
     unsigned long long cnt_lo = 0, cnt_hi = 0;
     unsigned int open_roots = 0;   // clusters reaching a tile border, counted at their root
+    OpenTally tl;                  // labeling statistics of the root walks
     int cur = -1;
     static_assert(kCodeClosed == kOpenSlots && SW_MAX_Q <= 128, "codes index the table");
     for (int k = threadIdx.x; k < SW_MAX_Q; k += blockDim.x) tab[kOpenSlots + k] = (unsigned char)k;
     auto flush = [&]() {
+        if (STATS && cur >= 0) flush_open_tally<kBlockThreads>(lat.stats, tl, 0u, red);
+        tl = OpenTally();
         if (MEASURE && cur >= 0) {
             block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass + 1, open_roots, red);
             if (lat.q == 2) {
@@ -1141,7 +1182,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
             const int cap = lat.dbg_loop_cap > 0 ? lat.dbg_loop_cap : lat.tiles_x * lat.tiles_y * kOpenSlots + 1;
             for (int s = threadIdx.x; s < n; s += blockDim.x) {
                 const uint32_t x = (uint32_t)tile * kOpenSlots + (uint32_t)s;
-                const unsigned long long e = find_open(lat.opar, x, cap, lat.st);
+                const unsigned long long e = find_open(lat.opar, x, cap, lat.st, tl);
                 const uint32_t key = (uint32_t)(e >> 32);
                 if (MEASURE && (uint32_t)e == x) ++open_roots;
                 const uint32_t u = draw4(lat, key, ctx.t, kTagState).x;
@@ -1378,14 +1419,19 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
     mark();
     const int mblocks =
         (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * shape.merge));
-    k_merge<<<mblocks, 256, 0, s>>>(b);
+    if (b.any_stats)
+        k_merge<true><<<mblocks, 256, 0, s>>>(b);
+    else
+        k_merge<false><<<mblocks, 256, 0, s>>>(b);
     mark();
     const int fblocks = std::max(
         1, std::min(b.ntasks, sm_count * std::min(shape.flip, b.any_clock ? kFlipResidentClock : kFlipResidentPotts)));
     if (b.any_clock)
-        k_flip_tiles<MEASURE, LABELS, true><<<fblocks, kBlockThreads, 0, s>>>(b);
+        b.any_stats ? k_flip_tiles<MEASURE, LABELS, true, true><<<fblocks, kBlockThreads, 0, s>>>(b)
+                    : k_flip_tiles<MEASURE, LABELS, true, false><<<fblocks, kBlockThreads, 0, s>>>(b);
     else
-        k_flip_tiles<MEASURE, LABELS, false><<<fblocks, kBlockThreads, 0, s>>>(b);
+        b.any_stats ? k_flip_tiles<MEASURE, LABELS, false, true><<<fblocks, kBlockThreads, 0, s>>>(b)
+                    : k_flip_tiles<MEASURE, LABELS, false, false><<<fblocks, kBlockThreads, 0, s>>>(b);
     mark();
     return cudaGetLastError();
 }

@@ -1,10 +1,12 @@
 """Temperature scans on the GPU engine (Komura & Okabe, arXiv:1202.0635,
 Sec. 4): the moment ratio U(T) = <M^4>/<M^2>^2 of several sizes (Eq. U; the
-crossing of the curves marks the critical point, Fig. 4), the time per spin
-flip against T with its per-stage split (Figs. 3 and 5), the correlation
-ratio R(T) = G(L/2)/G(L/4) of the clock model (Fig. 6), and the time per
-spin flip over the paper's grid of models and sizes, with and without the
-measurement (the two rows of its timing tables).
+crossing of the curves marks the critical point, Fig. 4), with jackknife
+errors of U and of the crossing temperature, the time per spin flip against
+T with its per-stage split (Figs. 3 and 5), the labeling statistics against
+T (the counterpart of the paper's count of labeling passes), the
+correlation ratio R(T) = G(L/2)/G(L/4) of the clock model (Fig. 6), and the
+time per spin flip over the paper's grid of models and sizes, with and
+without the measurement (the two rows of its timing tables).
 
 Every (L, T) point is its own lattice; all of them advance together in one
 batch (one launch sequence per sweep), so a scan costs about as much as
@@ -16,6 +18,8 @@ import argparse
 import importlib
 import json
 import math
+
+import numpy as np
 
 from . import workloads
 
@@ -58,6 +62,86 @@ def scan(q, model, sizes, temps, sweeps, equil=200, seed=1):
         return out
     finally:
         b.close()
+
+
+def m2_of_counts(counts, L, q):
+    """Per-sweep m^2 = M^2 / N^2 of the Potts model from the state counts
+    n_k (columns 0 .. q-1 of the counter rows), M^2 = (q sum n_k^2 - N^2) /
+    (q - 1) (Sec. 4, Eq. M^2)."""
+    n = np.asarray(counts, dtype=np.float64)[:, :q]
+    N = float(L) * float(L)
+    return (q * (n * n).sum(axis=1) - N * N) / (q - 1) / (N * N)
+
+
+def binder_scan(q, sizes, temps, sweeps, equil=500, seed=1, nbins=20):
+    """Potts moment ratio U = <m^4>/<m^2>^2 (Eq. U; m^4 = (m^2)^2) of every
+    (L, T) lattice with the per-sweep values kept: dict (L, T) -> array of
+    per-bin means of (m^2, m^4), nbins bins of the measured sweeps."""
+    sw = _sw()
+    b = sw.Batch()
+    try:
+        lats = {}
+        for i, L in enumerate(sizes):
+            for j, T in enumerate(temps):
+                lats[(L, T)] = b.add(L, q, sw.SW_POTTS, T, seed + 1000 * i + j, init=sw.SW_INIT_RANDOM)
+        sw.sw_batch_set_graph(b.b, 1)
+        b.sweep(equil)
+        for lat in lats.values():
+            lat.measure()
+            sw.sw_set_record(lat.h, 1)
+        b.sweep(sweeps)
+        out = {}
+        for (L, T), lat in lats.items():
+            m2 = m2_of_counts(lat.take_counts(sweeps + 1), L, q)
+            m = len(m2) // nbins * nbins
+            out[(L, T)] = np.stack([m2[:m].reshape(nbins, -1).mean(axis=1),
+                                    (m2[:m] ** 2).reshape(nbins, -1).mean(axis=1)], axis=1)
+        return out
+    finally:
+        b.close()
+
+
+def binder_crossing(bins, small, large, temps):
+    """Crossing temperature of U(T) of two sizes and its jackknife error
+    (leave one bin out of every lattice's series): (T, sigma_T) or (None, None)."""
+    def crossing_of(sel):
+        rows = []
+        for L in (small, large):
+            for T in temps:
+                b = bins[(L, T)][sel]
+                m2, m4 = b[:, 0].mean(), b[:, 1].mean()
+                rows.append({"L": L, "T": T, "U": m4 / (m2 * m2)})
+        return crossing(rows, "U", small, large)
+    nb = next(iter(bins.values())).shape[0]
+    full = crossing_of(np.arange(nb))
+    if full is None:
+        return None, None
+    jk = [crossing_of(np.delete(np.arange(nb), k)) for k in range(nb)]
+    if any(t is None for t in jk):
+        return full, None
+    jk = np.array(jk)
+    return full, float(math.sqrt((nb - 1) / nb * ((jk - jk.mean()) ** 2).sum()))
+
+
+def labeling_vs_T(q, model, L, temps, sweeps=50, equil=100, seed=1):
+    """Labeling statistics of one lattice at each T (sw_get_labeling_stats):
+    tile components, provisional labels and union pairs per tile, unions
+    across tile edges, and the walks of the global union-find."""
+    sw = _sw()
+    out = []
+    for T in temps:
+        lat = sw.Lattice(L, q, model, T, seed, init=sw.SW_INIT_RANDOM)
+        try:
+            sw.sw_set_graph(lat.h, 1)
+            lat.sweep(equil)
+            sw.sw_set_labeling_stats(lat.h, 1)
+            lat.sweep(sweeps)
+            row = {"T": T}
+            row.update(sw.sw_get_labeling_stats(lat.h))
+            out.append(row)
+        finally:
+            lat.close()
+    return out
 
 
 def crossing(rows, key, small, large):
@@ -149,11 +233,19 @@ def main():
     ap.add_argument("--n", type=int, default=9)
     ap.add_argument("--timing-L", type=int, default=1024)
     ap.add_argument("--matrix", action="store_true", help="only the ns/flip grid of models and sizes")
+    ap.add_argument("--labeling", action="store_true",
+                    help="only the labeling statistics against T at --timing-L (Potts q = 2, 3; clock q = 6)")
     args = ap.parse_args()
     sw = _sw()
     sw.lib()
     if args.matrix:
         print(json.dumps({"ns_per_flip": timing_matrix()}))
+        return
+    if args.labeling:
+        res = {}
+        for name, q, model in (("potts_q2", 2, sw.SW_POTTS), ("potts_q3", 3, sw.SW_POTTS), ("clock_q6", 6, sw.SW_CLOCK)):
+            res[name] = labeling_vs_T(q, model, args.timing_L, temperatures(q, model, 0.7, 1.3, 7))
+        print(json.dumps({"L": args.timing_L, "labeling": res}))
         return
     model = sw.SW_CLOCK if args.model == "clock" else sw.SW_POTTS
     temps = temperatures(args.q, model, args.lo, args.hi, args.n)

@@ -1,6 +1,7 @@
 """Physics of the GPU engine beyond the oracle's sizes (needs a GB300): the
-moment ratio U of Eq. (U) for L = 32 and 64 crosses at the exact critical
-point T_c = 1/ln(1 + sqrt q) of the Potts model (Sec. 4, Fig. 3)."""
+moment ratio U of Eq. (U) for L = 64 and 128 crosses at the exact critical
+point T_c = 1/ln(1 + sqrt q) of the Potts model (Sec. 4, Fig. 4), within the
+crossing's own jackknife error; the labeling statistics against T."""
 import pytest
 
 import paper_1202_0635_gb300 as sw
@@ -17,21 +18,21 @@ def built():
 
 
 @pytest.mark.parametrize("q", [2, 3])
-def test_binder_curves_cross_at_the_potts_critical_point(q):
-    temps = studies.temperatures(q, workloads.POTTS, 0.9, 1.1, 9)
-    rows = studies.scan(q, sw.SW_POTTS, [32, 64], temps, sweeps=6000, equil=300)
+def test_binder_crossing_of_64_and_128_is_the_potts_critical_point(q):
+    """U(T) of L = 64 and 128 from 20000 sweeps per point: the first crossing
+    scanning up in T lies within four jackknife errors (leave one of 20 bins
+    out) of the exact T_c, plus 0.1 pct of T_c for the crossing's own
+    finite-size shift at these sizes, and the scan pins T_c to half a pct."""
     tc = workloads.critical_temperature(q, workloads.POTTS)
+    temps = [tc * (0.97 + 0.0075 * k) for k in range(9)]
+    bins = studies.binder_scan(q, [64, 128], temps, sweeps=20000, equil=1000, nbins=20)
+    t, sig = studies.binder_crossing(bins, 64, 128, temps)
+    assert t is not None and sig is not None
+    assert abs(t - tc) <= 4.0 * sig + 1e-3 * tc, (t, sig, tc)
+    assert sig < 5e-3 * tc, (t, sig, tc)
     # Ordered side: U of the larger lattice is closer to 1.
-    lo = {r["L"]: r["U"] for r in rows if r["T"] == temps[0]}
-    assert lo[64] < lo[32]
-    if q == 2:   # the Ising limit U = 3 is approached from below above T_c
-        hi = {r["L"]: r["U"] for r in rows if r["T"] == temps[-1]}
-        assert hi[64] > hi[32]
-    # The first crossing scanning up in T is the critical point.  (For q = 3
-    # the disordered limit U = 2 is approached from above, so the curves
-    # cross once more further above T_c.)
-    t = studies.crossing(rows, "U", 32, 64)
-    assert t is not None and abs(t - tc) < 0.03 * tc, (t, tc)
+    u = {L: bins[(L, temps[0])][:, 1].mean() / bins[(L, temps[0])][:, 0].mean() ** 2 for L in (64, 128)}
+    assert u[128] < u[64]
 
 
 def test_timing_matrix_covers_the_grid():
@@ -42,3 +43,14 @@ def test_timing_matrix_covers_the_grid():
     assert {(r["model"], r["q"]) for r in rows} == {("potts", 2), ("potts", 3), ("potts", 4), ("clock", 6)}
     for r in rows:
         assert r["update_only"] > 0.0 and r["with_measurement"] > 0.0
+
+
+def test_labeling_statistics_against_temperature():
+    """The open components per tile fall below T_c, where one cluster spans
+    the lattice, and the tile components grow towards high T."""
+    tc = workloads.critical_temperature(2, workloads.POTTS)
+    rows = studies.labeling_vs_T(2, sw.SW_POTTS, 256, [0.7 * tc, tc, 1.3 * tc], sweeps=5, equil=20)
+    assert [r["sweeps"] for r in rows] == [5, 5, 5]
+    comps = [r["components_per_tile"] for r in rows]
+    assert comps[0] < comps[1] < comps[2]
+    assert rows[0]["open_per_tile"] < rows[2]["open_per_tile"]

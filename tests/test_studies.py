@@ -24,3 +24,29 @@ def test_crossing_of_two_straight_lines():
 def test_no_crossing_gives_none():
     rows = [{"L": 16, "T": T, "U": 2.0} for T in (1.0, 2.0)] + [{"L": 32, "T": T, "U": 1.0} for T in (1.0, 2.0)]
     assert studies.crossing(rows, "U", 16, 32) is None
+
+
+def test_m2_of_counts_limits():
+    import numpy as np
+    L, q = 6, 3
+    ordered = np.array([[36, 0, 0]])        # every site in one state: m^2 = 1
+    uniform = np.array([[12, 12, 12]])      # equal counts: M^2 = 0
+    assert studies.m2_of_counts(ordered, L, q)[0] == pytest.approx(1.0)
+    assert studies.m2_of_counts(uniform, L, q)[0] == pytest.approx(0.0)
+
+
+def test_binder_crossing_and_its_jackknife_error():
+    """Synthetic bins whose U(T) are straight lines crossing at T = 1: the
+    crossing is found there, and bins that scatter give a positive error."""
+    import numpy as np
+    temps = [0.8, 0.9, 1.05, 1.2]
+    rng = np.random.default_rng(0)
+    bins = {}
+    for L, slope in ((16, 1.0), (32, 3.0)):
+        for T in temps:
+            u = 1.0 + slope * (T - 1.0) + 2.0   # both equal 3 at T = 1
+            m2 = 0.5 * (1.0 + 1e-3 * rng.standard_normal(20))
+            bins[(L, T)] = np.stack([m2, u * m2.mean() ** 2 * np.ones(20)], axis=1)
+    t, sig = studies.binder_crossing(bins, 16, 32, temps)
+    assert t == pytest.approx(1.0, abs=5e-3)
+    assert sig is not None and 0.0 < sig < 0.05
