@@ -1627,6 +1627,13 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     SW_CUDA(cudaStreamSynchronize(s));
     if (nbad) return fail(SW_ERR_ARG, "%u spins outside [0, %d); nothing was changed", nbad, q);
 
+    // Once sweeps are enqueued, an error return first waits (best effort) for
+    // the work already on the stream, so that no later call's work can
+    // overlap it in the shared array.
+    auto settle_fail = [&](int rc) {
+        cudaStreamSynchronize(s);
+        return rc;
+    };
     // Sweeps in chunks that fit the counter rows; after each chunk the
     // newest configuration's bond classes are completed and the chunk's rows
     // copied to d_counts (row k = sweep sweep0 + k).
@@ -1635,20 +1642,21 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
         const int c = std::min(n - done, kNoallocRingSlots - 1);
         for (int k = 0; k < c; ++k) {
             e = swgb::launch_sweep(b, measure, false, sms, shape, s);
-            if (e != cudaSuccess) return cuda_fail(e, "launch_sweep");
+            if (e != cudaSuccess) return settle_fail(cuda_fail(e, "launch_sweep"));
         }
         if (measure) {
             e = swgb::launch_pending_classes(lat, sms, s);
-            if (e != cudaSuccess) return cuda_fail(e, "launch_pending_classes");
+            if (e != cudaSuccess) return settle_fail(cuda_fail(e, "launch_pending_classes"));
             const uint64_t t0 = sweep0 + (uint64_t)done;
             const size_t first = (size_t)(t0 % kNoallocRingSlots);
             const size_t n1 = std::min((size_t)c, (size_t)kNoallocRingSlots - first);
             const size_t row = (size_t)nc * sizeof(unsigned long long);
-            SW_CUDA(cudaMemcpyAsync(d_counts + (size_t)done * nc, lat.ring + first * nc, n1 * row,
-                                    cudaMemcpyDeviceToDevice, s));
-            if (n1 < (size_t)c)
-                SW_CUDA(cudaMemcpyAsync(d_counts + ((size_t)done + n1) * nc, lat.ring, ((size_t)c - n1) * row,
-                                        cudaMemcpyDeviceToDevice, s));
+            e = cudaMemcpyAsync(d_counts + (size_t)done * nc, lat.ring + first * nc, n1 * row,
+                                cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess && n1 < (size_t)c)
+                e = cudaMemcpyAsync(d_counts + ((size_t)done + n1) * nc, lat.ring, ((size_t)c - n1) * row,
+                                    cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return settle_fail(cuda_fail(e, "cudaMemcpyAsync(counters)"));
         }
         done += c;
     }

@@ -54,6 +54,9 @@ CASES = [
     (64, 2, sw.SW_ISING, TC_ISING, 11, 7, 5),
     (100, 3, sw.SW_POTTS, tc_potts(3), 12, 9, 300),
     (52, 6, sw.SW_CLOCK, 0.9, 13, 6, 6),
+    # The clock model's class and correlation counters through the chunked
+    # drain (n2 > 127 rows).
+    (40, 6, sw.SW_CLOCK, 0.9, 15, 5, 260),
 ]
 
 
@@ -73,6 +76,26 @@ def test_two_calls_in_a_row_equal_sw_sweep(L, q, model, T, seed, n1, n2):
         assert np.array_equal(spins.cpu().numpy().reshape(L, L), ref.spins), "spins differ at sweep %d" % sweep0
         assert np.array_equal(counts.cpu().numpy(), want_rows), "counters differ at sweep %d" % sweep0
     ref.close()
+
+
+def test_repeated_calls_allocate_nothing():
+    """After a first call (which looks up the array's address and may load the
+    library's code onto the device), further calls leave the device's free
+    memory and torch's allocator unchanged."""
+    L, q, model, T, seed = 256, 3, sw.SW_POTTS, tc_potts(3), 17
+    nc = sw.sw_ncounters(q, model)
+    spins = torch.zeros(L * L, dtype=torch.int8, device="cuda")
+    counts = torch.zeros((200, nc), dtype=torch.int64, device="cuda")
+    noalloc(L, q, model, T, seed, 0, 20, spins, counts)
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    sweep0 = 20
+    for n in (200, 1, 37):
+        noalloc(L, q, model, T, seed, sweep0, n, spins, counts)
+        sweep0 += n
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
 
 
 def test_without_counters_the_chain_is_unchanged():
