@@ -179,6 +179,15 @@ int sw_get_thresholds(sw_handle *h, uint32_t *out, int n);
 int sw_get_sweep(sw_handle *h, uint64_t *out);
 int sw_set_sweep(sw_handle *h, uint64_t t);
 
+/* Sweep limit: the lattice sweeps only while its sweep index is below
+ * `stop` (UINT64_MAX, the default: no limit).  Sweeps requested beyond it
+ * are skipped on the device -- in a batch every kernel leaves the lattice
+ * as it is -- and its index stays at `stop`, so a batch can be advanced by
+ * more sweeps than some of its lattices still need (a job server gives each
+ * job its budget this way).  sw_get_sweep_limit reads it back. */
+int sw_set_sweep_limit(sw_handle *h, uint64_t stop);
+int sw_get_sweep_limit(sw_handle *h, uint64_t *out);
+
 /* Launch shape: resident blocks per SM requested for the four kernels of
  * a sweep, shape[4] = {labeling, merge, flip, bonds}, each in [1, 64]
  * (default {8, 16, 10, 16}; the flip grid never exceeds the blocks its

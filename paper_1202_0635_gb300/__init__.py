@@ -89,6 +89,8 @@ EXPORTS = [
     ("sw_autotune", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("sw_set_launch_shape", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     ("sw_set_debug_limits", ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    ("sw_set_sweep_limit", ctypes.c_int, [_H, ctypes.c_uint64]),
+    ("sw_get_sweep_limit", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint64)]),
     ("sw_set_labeling_stats", ctypes.c_int, [_H, ctypes.c_int]),
     ("sw_get_labeling_stats", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("sw_batch_create", ctypes.c_void_p, [ctypes.c_void_p]),
@@ -329,6 +331,16 @@ def sw_batch_profile_sweeps(b, n):
     out = np.zeros(8, dtype=np.float32)
     m = _check(lib().sw_batch_profile_sweeps(b, int(n), _p(out, ctypes.c_float), 8))
     return [float(v) for v in out[:m]]
+
+
+def sw_set_sweep_limit(h, stop):
+    return _check(lib().sw_set_sweep_limit(h, ctypes.c_uint64(int(stop))))
+
+
+def sw_get_sweep_limit(h):
+    out = ctypes.c_uint64(0)
+    _check(lib().sw_get_sweep_limit(h, ctypes.byref(out)))
+    return int(out.value)
 
 
 def sw_set_debug_limits(h, loop_cap, list_cap):

@@ -19,6 +19,7 @@
 #include "sw_internal.h"
 
 using swgb::Batch;
+using swgb::BatchSizes;
 using swgb::DevState;
 using swgb::LaunchShape;
 using swgb::Lattice;
@@ -90,6 +91,7 @@ struct sw_handle {
     unsigned long long *d_ring = nullptr;
     // Batch-of-one view used by sw_sweep: descriptor, task / merge prefixes, ticket.
     Lattice *d_self = nullptr;
+    BatchSizes *d_sizes = nullptr;
     int *d_task_off = nullptr;
     long long *d_merge_off = nullptr;
     unsigned int *d_ticket = nullptr;
@@ -112,6 +114,7 @@ struct sw_handle {
     bool measure = true, labels = false, record = false, use_graph = false;
     LaunchShape shape;
     uint64_t t_host = 0;       // sweep index after all enqueued work
+    uint64_t stop = swgb::kNoStop;   // sweeps run only while the index is below this (sw_set_sweep_limit)
     uint64_t t_drained = 0;    // first sweep whose counters are still on the device
     int sticky = SW_OK;
     std::string sticky_msg;
@@ -163,6 +166,7 @@ struct sw_handle {
     Batch self_batch() const
     {
         Batch b{};
+        b.dev = d_sizes;
         b.lat = d_self;
         b.task_off = d_task_off;
         b.merge_off = d_merge_off;
@@ -187,6 +191,7 @@ struct sw_batch {
     LaunchShape shape;
     // device descriptor arrays (capacity grows; contents rewritten on change)
     int cap = 0;
+    BatchSizes *d_sizes = nullptr;   // the kernels read the sizes here (no recapture when they change)
     Lattice *d_lat = nullptr;
     int *d_task_off = nullptr;
     long long *d_merge_off = nullptr;
@@ -202,10 +207,12 @@ struct sw_batch {
     Batch view() const
     {
         Batch b{};
+        b.dev = d_sizes;
         b.lat = d_lat;
         b.task_off = d_task_off;
         b.merge_off = d_merge_off;
         b.ticket = d_ticket;
+        b.full_grid = 1;
         b.nrep = nrep;
         b.ntasks = ntasks;
         b.nmerge = nmerge;
@@ -365,6 +372,7 @@ int reset_device_index(sw_handle *h, uint64_t t)
 {
     DevState st{};
     st.sweep = t;
+    st.stop = h->stop;
     st.classes_upto = t;   // the current configuration is not a sweep result of this run
     SW_CUDA(cudaMemcpyAsync(h->d_st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
     SW_CUDA(cudaMemsetAsync(h->d_ring, 0, sizeof(unsigned long long) * swgb::kRingSlots * h->ncounters, h->stream));
@@ -545,6 +553,7 @@ void free_handle(sw_handle *h)
     if (h->d_stats) cudaFree(h->d_stats);
     if (h->d_self) cudaFree(h->d_self);
     if (h->d_task_off) cudaFree(h->d_task_off);
+    if (h->d_sizes) cudaFree(h->d_sizes);
     if (h->d_merge_off) cudaFree(h->d_merge_off);
     if (h->d_ticket) cudaFree(h->d_ticket);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -661,6 +670,10 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
         if ((e = cudaMalloc(&h->d_task_off, sizeof task_off)) != cudaSuccess) return bail(e, "cudaMalloc(tasks)");
         if ((e = cudaMalloc(&h->d_merge_off, sizeof merge_off)) != cudaSuccess) return bail(e, "cudaMalloc(merge)");
         if ((e = cudaMalloc(&h->d_ticket, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMalloc(ticket)");
+        const BatchSizes sizes{1, h->ntasks(), h->nmerge()};
+        if ((e = cudaMalloc(&h->d_sizes, sizeof sizes)) != cudaSuccess) return bail(e, "cudaMalloc(sizes)");
+        if ((e = cudaMemcpy(h->d_sizes, &sizes, sizeof sizes, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy(sizes)");
         if ((e = cudaMemcpy(h->d_self, &self, sizeof self, cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(e, "cudaMemcpy(descriptor)");
         if ((e = cudaMemcpy(h->d_task_off, task_off, sizeof task_off, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -721,7 +734,7 @@ int sw_sweep(sw_handle *h, int n)
     if (!h) return fail(SW_ERR_ARG, "null handle");
     if (n < 0) return fail(SW_ERR_ARG, "n=%d < 0", n);
     if (h->sticky != SW_OK) return fail(h->sticky, "%s", h->sticky_msg.c_str());
-    for (int s = 0; s < n; ++s) {
+    for (int s = 0; s < n && h->t_host < h->stop; ++s) {
         if (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) {
             int rc = drain(h);
             if (rc != SW_OK) return rc;
@@ -947,7 +960,7 @@ int sw_profile_sweeps(sw_handle *h, int n, float *ms, int max_stages)
             return (h->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) ? drain(h) : (int)SW_OK;
         },
         [&]() {
-            h->t_host++;
+            if (h->t_host < h->stop) h->t_host++;   // skipped at its limit
             if (!h->measure) h->t_drained = h->t_host;
         });
     if (rc != SW_OK) return rc;
@@ -984,7 +997,7 @@ int sw_autotune(sw_handle *h, int n, int *shape_out)
                                                                                                        : (int)SW_OK;
                 },
                 [&]() {
-                    h->t_host++;
+                    if (h->t_host < h->stop) h->t_host++;   // skipped at its limit
                     if (!h->measure) h->t_drained = h->t_host;
                 });
         });
@@ -1108,6 +1121,24 @@ int sw_get_labeling_stats(sw_handle *h, double *out, int n)
     return m;
 }
 
+int sw_set_sweep_limit(sw_handle *h, uint64_t stop)
+{
+    if (!h) return fail(SW_ERR_ARG, "null handle");
+    int rc = drain(h);
+    if (rc != SW_OK) return rc;
+    h->stop = stop;
+    SW_CUDA(cudaMemcpyAsync(&h->d_st->stop, &h->stop, sizeof h->stop, cudaMemcpyHostToDevice, h->stream));
+    SW_CUDA(cudaStreamSynchronize(h->stream));
+    return SW_OK;
+}
+
+int sw_get_sweep_limit(sw_handle *h, uint64_t *out)
+{
+    if (!h || !out) return fail(SW_ERR_ARG, "null argument");
+    *out = h->stop;
+    return SW_OK;
+}
+
 int sw_set_graph(sw_handle *h, int on)
 {
     if (!h) return fail(SW_ERR_ARG, "null handle");
@@ -1164,15 +1195,17 @@ static int rebuild_batch(sw_batch *b)
         any_clock = any_clock || b->reps[i]->model == SW_CLOCK;
         any_stats = any_stats || b->reps[i]->d_stats != nullptr;
     }
-    // A captured graph holds the kernel parameters of the batch view.
-    if (task_off[n] != b->ntasks || merge_off[n] != b->nmerge || any_clock != b->any_clock ||
-        any_stats != b->any_stats || n != b->nrep)
-        drop_batch_graph(b);
+    // A captured graph holds the kernel parameters of the batch view: the
+    // arrays' addresses (reallocated above) and the variant flags; the sizes
+    // are read from device memory.
+    if (any_clock != b->any_clock || any_stats != b->any_stats) drop_batch_graph(b);
     b->any_stats = any_stats;
     b->ntasks = task_off[n];
     b->nmerge = merge_off[n];
     b->any_clock = any_clock;
     b->nrep = n;
+    const BatchSizes sizes{n, task_off[n], merge_off[n]};
+    SW_CUDA(cudaMemcpyAsync(b->d_sizes, &sizes, sizeof sizes, cudaMemcpyHostToDevice, b->stream));
     if (n) {
         SW_CUDA(cudaMemcpyAsync(b->d_lat, lat.data(), sizeof(Lattice) * n, cudaMemcpyHostToDevice, b->stream));
         SW_CUDA(cudaMemcpyAsync(b->d_task_off, task_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
@@ -1199,7 +1232,7 @@ static int batch_timed_sweeps(sw_batch *b, const LaunchShape &shape, int n, doub
         },
         [&]() {
             for (sw_handle *h : b->reps) {
-                h->t_host++;
+                if (h->t_host < h->stop) h->t_host++;   // skipped at its limit
                 if (!b->measure) h->t_drained = h->t_host;
             }
         });
@@ -1223,11 +1256,14 @@ sw_batch *sw_batch_create(void *stream)
             b->own_stream = (e == cudaSuccess);
         }
     }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sizes, sizeof(BatchSizes));
+    if (e == cudaSuccess) e = cudaMemset(b->d_sizes, 0, sizeof(BatchSizes));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(b->d_ticket, 0, sizeof(unsigned int));
     if (e != cudaSuccess) {
         cuda_fail(e, "sw_batch_create");
         if (b->d_ticket) cudaFree(b->d_ticket);
+        if (b->d_sizes) cudaFree(b->d_sizes);
         if (b->own_stream) cudaStreamDestroy(b->stream);
         delete b;
         return nullptr;
@@ -1243,6 +1279,7 @@ int sw_batch_destroy(sw_batch *b)
     drop_batch_graph(b);
     free_batch_arrays(b);
     if (b->d_ticket) cudaFree(b->d_ticket);
+    if (b->d_sizes) cudaFree(b->d_sizes);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return SW_OK;
@@ -1269,8 +1306,7 @@ int sw_batch_attach(sw_batch *b, sw_handle *h)
     drop_graph(h);
     h->owner = b;
     b->reps.push_back(h);
-    b->dirty = true;
-    drop_batch_graph(b);
+    b->dirty = true;   // descriptors rewritten before the next sweep; a captured sweep stays valid
     return SW_OK;
 }
 
@@ -1288,8 +1324,7 @@ int sw_batch_detach(sw_batch *b, sw_handle *h)
         h->own_stream = true;
     }
     drop_graph(h);
-    b->dirty = true;
-    drop_batch_graph(b);
+    b->dirty = true;   // descriptors rewritten before the next sweep; a captured sweep stays valid
     return rc;
 }
 
@@ -1309,18 +1344,21 @@ int sw_batch_sweep(sw_batch *b, int n)
         if (rc != SW_OK) return rc;
     }
     for (int s = 0; s < n; ++s) {
+        bool any = false;   // a lattice below its sweep limit
         for (sw_handle *h : b->reps) {
             if (h->sticky != SW_OK) return fail(h->sticky, "%s", h->sticky_msg.c_str());
             if (b->measure && h->t_host - h->t_drained >= (uint64_t)swgb::kRingSlots - 1) {
                 int rc = drain(h);
                 if (rc != SW_OK) return rc;
             }
+            any = any || h->t_host < h->stop;
         }
+        if (!any) break;
         int rc = enqueue_sweep(b->view(), b->measure, b->labels, b->sm_count, b->shape, b->stream, b->use_graph,
                                &b->graph, &b->graph_exec);
         if (rc != SW_OK) return rc;
         for (sw_handle *h : b->reps) {
-            h->t_host++;
+            if (h->t_host < h->stop) h->t_host++;   // the kernels skip a lattice at its limit
             if (!b->measure) h->t_drained = h->t_host;
         }
     }
@@ -1457,7 +1495,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the working buffers inside the shared array, sized for
 // the largest accepted lattice (SW_NOALLOC_MAX_L).
 struct NoallocLayout {
-    size_t code, opar, edge, open_count, cross, bond, ring, thr_tab, st, lat, task_off, merge_off, ticket, total;
+    size_t code, opar, edge, open_count, cross, bond, ring, thr_tab, st, lat, sizes, task_off, merge_off, ticket, total;
 };
 constexpr int kNoallocRingSlots = 128;   // counter rows; longer calls are drained in chunks
 
@@ -1478,6 +1516,7 @@ constexpr NoallocLayout noalloc_layout()
     o.thr_tab = at;    at = align256(at + (size_t)(2 * SW_MAX_CLOCK_Q) * (2 * SW_MAX_CLOCK_Q) * sizeof(uint32_t));
     o.st = at;         at = align256(at + sizeof(DevState));
     o.lat = at;        at = align256(at + sizeof(Lattice));
+    o.sizes = at;      at = align256(at + sizeof(BatchSizes));
     o.task_off = at;   at = align256(at + 2 * sizeof(int));
     o.merge_off = at;  at = align256(at + 2 * sizeof(long long));
     o.ticket = at;     at = align256(at + sizeof(unsigned int));
@@ -1594,6 +1633,7 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     const int task_off[2] = {0, tiles_x * tiles_y};
     const long long merge_off[2] = {0, (long long)tiles_x * tiles_y * swgb::kMergeItems};
     Batch b{};
+    b.dev = (const BatchSizes *)(base + kNoalloc.sizes);
     b.lat = (const Lattice *)(base + kNoalloc.lat);
     b.task_off = (const int *)(base + kNoalloc.task_off);
     b.merge_off = (const long long *)(base + kNoalloc.merge_off);
@@ -1608,11 +1648,14 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     // counter rows).  Labels, codes and open lists are written before read.
     DevState st{};
     st.sweep = sweep0;
+    st.stop = swgb::kNoStop;
     st.classes_upto = sweep0;
     SW_CUDA(cudaMemcpyAsync(lat.st, &st, sizeof st, cudaMemcpyHostToDevice, s));
     SW_CUDA(cudaMemsetAsync(b.ticket, 0, sizeof(unsigned int), s));
     SW_CUDA(cudaMemsetAsync(lat.ring, 0, sizeof(unsigned long long) * kNoallocRingSlots * nc, s));
     SW_CUDA(cudaMemcpyAsync(base + kNoalloc.lat, &lat, sizeof lat, cudaMemcpyHostToDevice, s));
+    const BatchSizes sizes{1, b.ntasks, b.nmerge};
+    SW_CUDA(cudaMemcpyAsync(base + kNoalloc.sizes, &sizes, sizeof sizes, cudaMemcpyHostToDevice, s));
     SW_CUDA(cudaMemcpyAsync(base + kNoalloc.task_off, task_off, sizeof task_off, cudaMemcpyHostToDevice, s));
     SW_CUDA(cudaMemcpyAsync(base + kNoalloc.merge_off, merge_off, sizeof merge_off, cudaMemcpyHostToDevice, s));
     if (!tab.empty())

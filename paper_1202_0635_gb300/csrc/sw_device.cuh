@@ -19,9 +19,12 @@ enum : int { kErrNone = 0, kErrFindCap = 1, kErrUnionCap = 2, kErrTimeBudget = 3
 // error and returns instead of spinning on.
 constexpr long long kLoopBudgetCycles = 2000000000ll;
 
+constexpr unsigned long long kNoStop = ~0ull;
+
 // Sticky per-lattice device state.
 struct DevState {
     unsigned long long sweep;          // sweeps completed; read by every kernel of a sweep
+    unsigned long long stop;           // the lattice sweeps only while sweep < stop (kNoStop: always)
     unsigned long long classes_upto;   // configurations < this index have their bond classes counted
     unsigned int ticket;               // blocks finished in the sweep's last kernel
     int err;                           // first device error (kErr*)
@@ -82,7 +85,16 @@ enum : int {
 // A set of lattices swept together; a single lattice is a batch of one.
 // One block task is one tile of one lattice, processed by kTaskWarps warps.
 constexpr int kTaskWarps = 4;
+// Sizes of a batch, in device memory: the kernels read them there, so a
+// captured sweep stays valid when lattices join or leave.
+struct BatchSizes {
+    int nrep;
+    int ntasks;
+    long long nmerge;
+};
+
 struct Batch {
+    const BatchSizes *dev;         // the sizes below, as the kernels read them (device memory)
     const Lattice *lat;            // [nrep] descriptors (device memory)
     const int *task_off;           // [nrep + 1] prefix sums of the lattices' tile counts
     const long long *merge_off;    // [nrep + 1] prefix sums of the lattices' merge items (kMergeItems a tile)
@@ -92,6 +104,7 @@ struct Batch {
     long long nmerge;
     int any_clock;                 // a clock lattice is present (selects the kernel variant that measures it)
     int any_stats;                 // a lattice gathers labeling statistics (selects the variants that tally)
+    int full_grid;                 // size every grid for the whole GPU, not for ntasks / nmerge (batches)
 };
 
 // Philox-4x32-10 (Salmon et al., SC'11).  Each round takes two 32x32->64

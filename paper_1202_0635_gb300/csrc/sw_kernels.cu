@@ -136,6 +136,7 @@ struct TaskCtx {
     unsigned long long t;   // sweep index
     int count_classes;      // bond classes of configuration t - 1 are counted now
     int m;                  // clock mirror axis
+    int active;             // the lattice sweeps this time (sweep index below its limit)
 };
 
 template <bool MEASURE>
@@ -143,7 +144,8 @@ __device__ __forceinline__ TaskCtx task_context(const Lattice &lat)
 {
     TaskCtx c;
     c.t = read_u64(&lat.st->sweep);
-    c.count_classes = MEASURE && c.t >= 1ull && c.t - 1ull >= read_u64(&lat.st->classes_upto);
+    c.active = c.t < read_u64(&lat.st->stop);
+    c.count_classes = c.active && MEASURE && c.t >= 1ull && c.t - 1ull >= read_u64(&lat.st->classes_upto);
     c.m = lat.clock ? clock_axis(lat, c.t) : 0;
     return c;
 }
@@ -388,8 +390,9 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
         __syncthreads();
     };
 
-    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
-        const int rep = find_rep(b.task_off, b.nrep, task);
+    const int nrep = __ldg(&b.dev->nrep), ntasks = __ldg(&b.dev->ntasks);
+    for (int task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const int rep = find_rep(b.task_off, nrep, task);
         if (rep != cur) {
             flush();
             load_lattice(&lat, b.lat + rep);
@@ -413,6 +416,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
             }
             cur = rep;
         }
+        if (!ctx.active) continue;   // past its sweep limit: left as it is (uniform in the block)
         const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
         const bool clock = ANY_CLOCK && lat.clock != 0;
@@ -645,8 +649,9 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
         __syncthreads();
     };
 
-    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
-        const int rep = find_rep(b.task_off, b.nrep, task);
+    const int nrep = __ldg(&b.dev->nrep), ntasks = __ldg(&b.dev->ntasks);
+    for (int task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const int rep = find_rep(b.task_off, nrep, task);
         if (rep != cur) {
             flush();
             load_lattice(&lat, b.lat + rep);
@@ -655,6 +660,7 @@ __global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
             __syncthreads();
             cur = rep;
         }
+        if (!ctx.active) continue;   // past its sweep limit: left as it is (uniform in the block)
         const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
         const bool clock = lat.clock != 0;
@@ -952,6 +958,7 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
     const unsigned lane = threadIdx.x & 31;
     OpenTally tl;           // labeling statistics of the warp's current lattice
     unsigned int unions = 0;
+    bool active = true;     // the current lattice sweeps this time
     // A warp's items all belong to one lattice at a time: its tallies go to
     // that lattice's statistics (warp sums) when it moves on or finishes.
     auto flush_warp = [&]() {
@@ -972,20 +979,24 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
     };
     // Every lattice has a multiple of kMergeItems items: a warp never spans
     // two lattices, and its trip count is uniform.
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < b.nmerge;
+    const int nrep = __ldg(&b.dev->nrep);
+    const long long nmerge = __ldg(&b.dev->nmerge);
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nmerge;
          base += (long long)gridDim.x * blockDim.x) {
         const long long k = base + lane;
-        bool ok = k < b.nmerge;
+        bool ok = k < nmerge;
         uint32_t a = 0, c2 = 0;
         if (ok) {
             if (k < lo || k >= hi) {
                 if (STATS && rep >= 0) flush_warp();   // uniform: the warp's items share a lattice
-                rep = find_rep(b.merge_off, b.nrep, k);
+                rep = find_rep(b.merge_off, nrep, k);
                 lo = __ldg(b.merge_off + rep);
                 hi = __ldg(b.merge_off + rep + 1);
                 lp = b.lat + rep;
+                active = read_u64(&lp->st->sweep) < read_u64(&lp->st->stop);
             }
             const Lattice &lat = *lp;
+            ok = active;
             const int L = lat.L;
             const int kk = (int)(k - lo);
             const int tile = kk / kMergeItems, e = kk % kMergeItems;
@@ -995,7 +1006,7 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
             const uint32_t *cw = lat.cross + (size_t)tile * kCrossWords;
             int sa = 0, sb = 0, nt;
             if (e < TH) {   // right edge, row e, into the next tile to the right
-                ok = e < th && ((__ldg(cw + (e >> 5)) >> (e & 31)) & 1u);
+                ok = ok && e < th && ((__ldg(cw + (e >> 5)) >> (e & 31)) & 1u);
                 nt = by * lat.tiles_x + (bx + 1 == lat.tiles_x ? 0 : bx + 1);
                 if (ok) {
                     sa = lat.edge[(size_t)tile * kEdgeBytes + e];
@@ -1003,7 +1014,7 @@ __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
                 }
             } else {        // bottom edge, column e - 64, into the next tile below
                 const int c = e - TH;
-                ok = c < tw && ((__ldg(cw + 2 + (c >> 5)) >> (c & 31)) & 1u);
+                ok = ok && c < tw && ((__ldg(cw + 2 + (c >> 5)) >> (c & 31)) & 1u);
                 const int yn = by + 1 == lat.tiles_y ? 0 : by + 1;
                 nt = yn * lat.tiles_x + bx;
                 if (ok) {
@@ -1050,9 +1061,11 @@ __device__ void finish_sweep(const Batch &b)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int r = threadIdx.x; r < b.nrep; r += blockDim.x) {
+    const int nrep = __ldg(&b.dev->nrep);
+    for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
         const Lattice &lt = b.lat[r];
         const unsigned long long t = read_u64(&lt.st->sweep);
+        if (t >= read_u64(&lt.st->stop)) continue;   // did not sweep this time
         const bool counted = MEASURE && t >= 1ull && t - 1ull >= read_u64(&lt.st->classes_upto);
         unsigned long long *next = ring_row(lt, t + 1);
         for (int c = 0; c < lt.ncounters; ++c) next[c] = 0ull;
@@ -1119,8 +1132,9 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
         open_roots = 0;
         __syncthreads();
     };
-    for (int task = blockIdx.x; task < b.ntasks; task += gridDim.x) {
-        const int rep = find_rep(b.task_off, b.nrep, task);
+    const int nrep = __ldg(&b.dev->nrep), ntasks = __ldg(&b.dev->ntasks);
+    for (int task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const int rep = find_rep(b.task_off, nrep, task);
         if (rep != cur) {
             flush();
             load_lattice(&lat, b.lat + rep);
@@ -1130,6 +1144,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
             __syncthreads();
             cur = rep;
         }
+        if (!ctx.active) continue;   // past its sweep limit: left as it is (uniform in the block)
         const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
         const bool clock = ANY_CLOCK && lat.clock != 0;   // ANY_CLOCK: the batch holds a clock lattice
@@ -1409,23 +1424,27 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
         if (ev) cudaEventRecord(ev[nev++], s);
     };
     mark();
-    const int bblocks = std::max(1, std::min(b.ntasks, sm_count * shape.bonds));
+    // Batches take the whole GPU's grid, whatever their current size, so that
+    // a captured sweep stays valid when lattices join or leave.
+    auto grid = [&](long long work, int per_sm) {
+        const long long cap = (long long)sm_count * per_sm;
+        return (int)std::max<long long>(1, b.full_grid ? cap : std::min(work, cap));
+    };
+    const int bblocks = grid(b.ntasks, shape.bonds);
     if (b.any_clock)
         k_bonds<MEASURE, true><<<bblocks, kBlockThreads, 0, s>>>(b);
     else
         k_bonds<MEASURE, false><<<bblocks, kBlockThreads, 0, s>>>(b);
     mark();
-    k_label_tiles<MEASURE, LABELS><<<std::max(1, std::min(b.ntasks, sm_count * shape.label)), kBlockThreads, 0, s>>>(b);
+    k_label_tiles<MEASURE, LABELS><<<grid(b.ntasks, shape.label), kBlockThreads, 0, s>>>(b);
     mark();
-    const int mblocks =
-        (int)std::max<long long>(1, std::min<long long>((b.nmerge + 255) / 256, (long long)sm_count * shape.merge));
+    const int mblocks = grid((b.nmerge + 255) / 256, shape.merge);
     if (b.any_stats)
         k_merge<true><<<mblocks, 256, 0, s>>>(b);
     else
         k_merge<false><<<mblocks, 256, 0, s>>>(b);
     mark();
-    const int fblocks = std::max(
-        1, std::min(b.ntasks, sm_count * std::min(shape.flip, b.any_clock ? kFlipResidentClock : kFlipResidentPotts)));
+    const int fblocks = grid(b.ntasks, std::min(shape.flip, b.any_clock ? kFlipResidentClock : kFlipResidentPotts));
     if (b.any_clock)
         b.any_stats ? k_flip_tiles<MEASURE, LABELS, true, true><<<fblocks, kBlockThreads, 0, s>>>(b)
                     : k_flip_tiles<MEASURE, LABELS, true, false><<<fblocks, kBlockThreads, 0, s>>>(b);

@@ -7,12 +7,15 @@ T, seed) from a random start, and gets back its running-mean observables
 
 Jobs are admitted first-come-first-served while their device memory fits
 the HBM budget; admitted lattices stay resident and are advanced together
-by one batched launch sequence per sweep (sw_batch).  Every engine step
-advances all resident jobs by the same number of sweeps -- the largest
-count that no job overshoots -- so a job that arrives while others run
-joins the next step and finished jobs leave at once (continuous batching).
-A job's chain depends only on its own parameters and seed, so its result is
-the same alone and in any mix.
+by one batched launch sequence per sweep (sw_batch).  Every lattice carries
+its job's sweep budget on the device (sw_set_sweep_limit), so every engine
+step advances all resident jobs by a full chunk of sweeps and a job whose
+budget runs out within the chunk simply stops there; a job that arrives
+while others run joins the next step and finished jobs leave after it
+(continuous batching).  Membership changes rewrite the batch's device
+descriptors without recapturing its CUDA graph.  A job's chain depends only
+on its own parameters and seed, so its result is the same alone and in any
+mix.
 
     python -m paper_1202_0635_gb300.serve [--jobs 1000] [--rate 200] [--budget-gb 120]
 """
@@ -28,15 +31,17 @@ from . import workloads
 
 
 def job_bytes(L, q, model):
-    """Device bytes one resident lattice holds (spins int8, codes uint16,
-    labels int32, per-tile bond masks / open lists / crossing words,
-    counter ring)."""
+    """Device bytes one resident lattice holds: spins int8 and codes uint16
+    per site; per 64 x 64 tile its bond masks (1 KB), open-component entries
+    (256 x 8 B), edge bytes, open count and crossing words; the counter ring,
+    the clock threshold table and the descriptors.  (Labels are allocated
+    only for debug labels, which the server does not use.)"""
     n = L * L
     tiles = ((L + 63) // 64) ** 2
     nclass = q // 2 + 1 if model == 1 else 2
     ring = 1024 * (q + nclass + 2 + (2 * nclass if model == 1 else 0)) * 8
     table = (2 * q) ** 2 * 4 if model == 1 else 0
-    return n * (1 + 2 + 4) + tiles * (1024 + 256 * 4 + 4 + 16) + ring + table + 4096
+    return n * (1 + 2) + tiles * (1024 + 256 * 8 + 128 + 4 + 16) + ring + table + 4096
 
 
 class GpuBackend:
@@ -52,6 +57,7 @@ class GpuBackend:
         sw = self.sw
         h = sw.sw_create(job["L"], job["q"], job["model"], job["T"], job["seed"])
         sw.sw_init(h, sw.SW_INIT_RANDOM)
+        sw.sw_set_sweep_limit(h, int(job["sweeps"]))
         sw.sw_batch_attach(self.b, h)
         return h
 
@@ -115,11 +121,12 @@ class Server:
         return admitted
 
     def chunk(self):
-        """Sweeps for the next engine step: the largest count no resident job
-        overshoots, at most max_chunk."""
+        """Sweeps for the next engine step: max_chunk, or fewer when every
+        resident job needs fewer (jobs stop at their own budget on the
+        device)."""
         if not self.active:
             return 0
-        return max(1, min(self.max_chunk, min(a[2] for a in self.active.values())))
+        return max(1, min(self.max_chunk, max(a[2] for a in self.active.values())))
 
     def step(self, now_fn):
         """Admit, advance every resident job, retire the finished ones."""
@@ -129,10 +136,11 @@ class Server:
             return 0
         self.backend.advance(k)
         self.steps += 1
-        self.sweeps_done += k * len(self.active)
         finished = []
         for jid, a in self.active.items():
-            a[2] -= k
+            done = min(k, a[2])
+            self.sweeps_done += done
+            a[2] -= done
             if a[2] == 0:
                 finished.append(jid)
         for jid in finished:

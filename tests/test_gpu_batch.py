@@ -164,3 +164,38 @@ def test_autotune_picks_a_cached_shape_and_keeps_the_chain():
     bshape = sw.sw_batch_autotune(b.b, 1)
     assert all(1 <= v <= 64 for v in bshape)
     b.close()
+
+
+def test_sweep_limits_stop_lattices_inside_a_captured_batch():
+    """Lattices with sweep limits 5, 9 and none advanced by one graph-launched
+    batch equal plain lattices swept 5, 9 and 12 times (spins and counter
+    rows); a lattice that joins after 7 sweeps with a limit of 3 does 3.  The
+    batch's captured sweep stays valid across the join."""
+    specs = [(64, 2, sw.SW_POTTS, 1.0 / math.log(1.0 + math.sqrt(2.0)), 5),
+             (100, 3, sw.SW_POTTS, 1.0 / math.log(1.0 + math.sqrt(3.0)), 9),
+             (48, 6, sw.SW_CLOCK, 0.9, None)]
+    b = sw.Batch()
+    sw.sw_batch_set_graph(b.b, 1)
+    lats = []
+    for i, (L, q, model, T, lim) in enumerate(specs):
+        lat = b.add(L, q, model, T, 300 + i, init=sw.SW_INIT_RANDOM)
+        if lim is not None:
+            sw.sw_set_sweep_limit(lat.h, lim)
+        sw.sw_set_record(lat.h, 1)
+        lats.append((lat, L, q, model, T, 300 + i, lim if lim is not None else 12))
+    b.sweep(7)
+    late = b.add(76, 4, sw.SW_POTTS, 1.0 / math.log(3.0), 399, init=sw.SW_INIT_RANDOM)
+    sw.sw_set_sweep_limit(late.h, 3)
+    sw.sw_set_record(late.h, 1)
+    lats.append((late, 76, 4, sw.SW_POTTS, 1.0 / math.log(3.0), 399, 3))
+    b.sweep(5)
+    for lat, L, q, model, T, seed, want in lats:
+        assert lat.sweep_index == want
+        ref = sw.Lattice(L, q, model, T, seed, init=sw.SW_INIT_RANDOM)
+        sw.sw_set_record(ref.h, 1)
+        ref.sweep(want)
+        assert np.array_equal(lat.spins, ref.spins)
+        assert np.array_equal(lat.take_counts(), ref.take_counts())
+        ref.close()
+    assert sw.sw_get_sweep_limit(late.h) == 3
+    b.close()

@@ -18,13 +18,17 @@ class OracleBackend:
     def open(self, job):
         o = Oracle(job["L"], job["q"], job["model"], job["T"], job["seed"], init="random")
         self.rows[id(o)] = []
+        self.limit = getattr(self, "limit", {})
+        self.limit[id(o)] = int(job["sweeps"])   # the device's per-lattice sweep limit
         self.live.append(o)
         self.opened.append(job["id"])
         return o
 
     def advance(self, k):
         for o in self.live:
-            self.rows[id(o)].append(o.sweep(k, record=True))
+            n = min(k, self.limit[id(o)] - o.sweep_index)
+            if n > 0:
+                self.rows[id(o)].append(o.sweep(n, record=True))
 
     def result(self, o, L):
         rows = np.concatenate(self.rows[id(o)])
