@@ -479,7 +479,7 @@ std::string tune_key(int nrep, int ntasks, long long nmerge, bool measure)
 template <typename Timer>
 int autotune_shape(LaunchShape *best, int n, Timer timer)
 {
-    static const int cand_label[] = {6, 8, 10};
+    static const int cand_label[] = {7, 9, 11};
     static const int cand_other[] = {4, 8, 16, 32};
     double ms[swgb::kMaxStages];
     // Timed stages: 0 bonds, 1 labeling, 2 merge, 3 flip.

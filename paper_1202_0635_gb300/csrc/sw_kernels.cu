@@ -617,7 +617,7 @@ struct RowMasks {
 //            to the tile's edge bytes.
 // ---------------------------------------------------------------------------
 template <bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kBlockThreads, 10) k_label_tiles(Batch b)
+__global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
 {
     // Node words: provisional label of every node, which for a label's own
     // first node is its union-find parent.
