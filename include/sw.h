@@ -17,9 +17,12 @@
  *   spins are int8 states 0..q-1 (clock: angle 2*pi*k/q).
  *   Random numbers: Philox-4x32-10, key = (seed lo32, seed hi32), counter =
  *   (index, sweep lo32, tag, sweep hi32); tag 0 bonds (index i>>1, lane
- *   2*(i&1)+direction), tag 1 cluster draw (index = root, lane 0), tag 2
- *   clock mirror axis (index 0, lane 0), tag 3 random start (index i,
- *   sweep 0, lane 0).  "sweep" counts the sweeps completed before the one
+ *   2*(i&1)+direction), tag 1 cluster draw of the Potts model with q > 2
+ *   (index = root, lane 0, new state mulhi(u, q)), tag 2 clock mirror axis
+ *   (index 0, lane 0), tag 3 random start (index i, sweep 0, lane 0), tag 4
+ *   one-bit cluster draw of the q = 2 Potts / Ising new state and of the
+ *   clock reflection flag (index = root >> 7; bit root & 31 of lane
+ *   (root >> 5) & 3).  "sweep" counts the sweeps completed before the one
  *   drawing.  mulhi(u, q) = (u * q) >> 32.
  *   A bond is active iff its draw u < an integer threshold
  *   floor(p * 2^32) (clamped to 2^32-1), p = -expm1(-x) evaluated in double:

@@ -52,7 +52,7 @@ void swo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-enum { TAG_BOND = 0, TAG_STATE = 1, TAG_AXIS = 2, TAG_INIT = 3 };
+enum { TAG_BOND = 0, TAG_STATE = 1, TAG_AXIS = 2, TAG_INIT = 3, TAG_STATE_BIT = 4 };
 
 static uint32_t draw(uint64_t seed, uint32_t index, uint64_t sweep, uint32_t tag, int lane)
 {
@@ -61,6 +61,17 @@ static uint32_t draw(uint64_t seed, uint32_t index, uint64_t sweep, uint32_t tag
     uint32_t out[4];
     swo_philox4x32_10(ctr, key, out);
     return out[lane];
+}
+
+/* One uniform bit per index: bit (index & 31) of lane (index >> 5) & 3 of
+ * the draw with counter index >> 7 (128 indices share one Philox call). */
+static int draw_bit(uint64_t seed, uint32_t index, uint64_t sweep, uint32_t tag)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {index >> 7, (uint32_t)(sweep & 0xffffffffu), tag, (uint32_t)(sweep >> 32)};
+    uint32_t out[4];
+    swo_philox4x32_10(ctr, key, out);
+    return (int)((out[(index >> 5) & 3u] >> (index & 31u)) & 1u);
 }
 
 static int mulhi_q(uint32_t u, int q)
@@ -294,16 +305,19 @@ static void label_clusters(swo *o)
 }
 
 /* Sec. 2 steps (v)-(vii) (Potts) and the reflection of Sec. 4 (clock):
- * one draw per cluster, keyed on its label. */
+ * one draw per cluster, keyed on its label.  A uniform new state among q
+ * (Potts) or a reflection with probability 1/2 (clock); where there are
+ * two outcomes (q = 2, clock) the draw is one uniform bit. */
 static void flip_clusters(swo *o)
 {
     for (int64_t r = 0; r < o->N; ++r) {
         if (o->label[r] != r) continue;
-        uint32_t u = draw(o->seed, (uint32_t)r, o->sweep, TAG_STATE, 0);
-        if (o->model == SWO_CLOCK)
-            o->newstate[r] = (int8_t)(u >> 31);
-        else
+        if (o->model == SWO_CLOCK || o->q == 2) {
+            o->newstate[r] = (int8_t)draw_bit(o->seed, (uint32_t)r, o->sweep, TAG_STATE_BIT);
+        } else {
+            uint32_t u = draw(o->seed, (uint32_t)r, o->sweep, TAG_STATE, 0);
             o->newstate[r] = (int8_t)mulhi_q(u, o->q);
+        }
     }
     for (int64_t i = 0; i < o->N; ++i) {
         int8_t v = o->newstate[o->label[i]];

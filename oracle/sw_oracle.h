@@ -28,9 +28,13 @@
  *   Philox-4x32-10 key = (seed & 0xffffffff, seed >> 32).
  *   counter = (index, sweep & 0xffffffff, tag, sweep >> 32) with
  *     tag 0 BOND : index = i >> 1; lane 2*(i & 1) + direction is site i's draw
- *     tag 1 STATE: index = cluster root; lane 0
+ *     tag 1 STATE: index = cluster root; lane 0 (Potts, q > 2: the new state
+ *                  is mulhi(u, q))
  *     tag 2 AXIS : index = 0; lane 0 (clock mirror axis of the sweep)
  *     tag 3 INIT : index = i; lane 0 (random start; sweep field 0)
+ *     tag 4 STATE_BIT: index = r >> 7 for cluster root r; the new state
+ *                  (Potts / Ising, q = 2) or reflection flag (clock) is bit
+ *                  r & 31 of lane (r >> 5) & 3
  *   "sweep" is the number of sweeps completed before the one drawing.
  *   bond active iff the 32-bit draw u < threshold (an integer, see below).
  *   mulhi(u, q) = (u * q) >> 32 maps a draw to [0, q).

@@ -9,7 +9,7 @@
 namespace swgb {
 
 // Random-number tags of the counter (index, sweep lo, tag, sweep hi).
-enum : uint32_t { kTagBond = 0, kTagState = 1, kTagAxis = 2, kTagInit = 3 };
+enum : uint32_t { kTagBond = 0, kTagState = 1, kTagAxis = 2, kTagInit = 3, kTagStateBit = 4 };
 
 // Error codes stored in the device state word (first error wins).
 enum : int { kErrNone = 0, kErrFindCap = 1, kErrUnionCap = 2, kErrTimeBudget = 3, kErrInternal = 4 };
@@ -132,6 +132,31 @@ __device__ __forceinline__ uint4 draw4(const Lattice &lat, uint32_t index, unsig
 __device__ __forceinline__ int mulhi_q(uint32_t u, int q)
 {
     return (int)__umulhi(u, (uint32_t)q);
+}
+
+// Bit r & 31 of lane (r >> 5) & 3 of the STATE_BIT draw with index r >> 7:
+// one uniform bit per index, 128 indices to a Philox call.
+__device__ __forceinline__ int draw_bit(const Lattice &lat, uint32_t r, unsigned long long t)
+{
+    const uint4 u = draw4(lat, r >> 7, t, kTagStateBit);
+    const uint32_t l = (r >> 5) & 3u;
+    const uint32_t w = l == 0 ? u.x : l == 1 ? u.y : l == 2 ? u.z : u.w;
+    return (int)((w >> (r & 31u)) & 1u);
+}
+
+// Does the cluster draw take one bit?  Two outcomes: the new state of the
+// q = 2 Potts (Ising) model, the reflection flag of the clock model.
+__device__ __forceinline__ bool bit_draw(const Lattice &lat)
+{
+    return lat.clock != 0 || lat.q == 2;
+}
+
+// The draw of the cluster rooted at site r (Sec. 2 (v)-(vii), Sec. 4): its
+// new state (Potts), uniform in [0, q), or its reflection flag (clock).
+__device__ __forceinline__ int cluster_draw(const Lattice &lat, uint32_t r, unsigned long long t)
+{
+    if (bit_draw(lat)) return draw_bit(lat, r, t);
+    return mulhi_q(draw4(lat, r, t, kTagState).x, lat.q);
 }
 
 // Mirror axis of the sweep (clock model).

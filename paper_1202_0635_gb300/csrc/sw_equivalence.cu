@@ -111,8 +111,8 @@ __global__ void k_eq_relabel(Lattice lat, const int32_t *R)
         lat.label[i] = R[lat.label[i]];
 }
 
-// New spins: every site takes its cluster root's draw (tag STATE, index =
-// root).  The clock reflection uses the sweep's mirror axis.
+// New spins: every site takes its cluster root's draw (cluster_draw).  The
+// clock reflection uses the sweep's mirror axis.
 template <bool CLOCK>
 __global__ void k_eq_flip(Lattice lat)
 {
@@ -121,14 +121,14 @@ __global__ void k_eq_flip(Lattice lat)
     const int q = lat.q;
     const int m = CLOCK ? clock_axis(lat, t) : 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t u = draw4(lat, (uint32_t)lat.label[i], t, kTagState).x;
+        const int d = cluster_draw(lat, (uint32_t)lat.label[i], t);
         if (CLOCK) {
             const int k = valid_state(lat.spin[i], q);
             int r = m - k;
             if (r < 0) r += q;
-            lat.spin[i] = (int8_t)((u >> 31) ? r : k);
+            lat.spin[i] = (int8_t)(d ? r : k);
         } else {
-            lat.spin[i] = (int8_t)mulhi_q(u, q);
+            lat.spin[i] = (int8_t)d;
         }
     }
 }

@@ -131,6 +131,16 @@ __device__ __forceinline__ void add_hist_any(unsigned int *hist, int v, bool val
     }
 }
 
+// The kernels of a sweep are launched with programmatic stream
+// serialization: the next kernel of the stream launches as this one's
+// blocks exit, and waits here until the previous kernel has completed and
+// its writes are visible.  Nothing before this point touches memory.
+// (Launched without the attribute, the wait does nothing.)
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Per-lattice values every block needs once per task.
 struct TaskCtx {
     unsigned long long t;   // sweep index
@@ -363,6 +373,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
+    pdl_begin();
     unsigned int active = 0, unequal = 0, pairs = 0;
     int cur = -1;
     // Counters of lattice `cur` -> its ring rows (whole block).
@@ -635,6 +646,7 @@ __global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
+    pdl_begin();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qx = warp & 1, qy = warp >> 1;
     const int row = QW * qy + lane;   // my tile row (lane = row phases)
@@ -663,7 +675,6 @@ __global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
         if (!ctx.active) continue;   // past its sweep limit: left as it is (uniform in the block)
         const int tile = task - __ldg(b.task_off + rep);
         const int L = lat.L, q = lat.q;
-        const bool clock = lat.clock != 0;
         const unsigned long long t = ctx.t;
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
         const int X0 = bx * TW, Y0 = by * TH;
@@ -836,6 +847,21 @@ __global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
         // ===== settle: every provisional label points at its root; a closed
         // root draws, an open root takes a slot.  A settled root's word is
         // resolved; walks stop there.
+        // One-bit cluster draws (bit_draw): the STATE_BIT bits of the tile's
+        // sites, eight words per tile row from the two draws that cover the
+        // row, in the room of the scan masks (free after the open phase).
+        uint32_t *bits = reinterpret_cast<uint32_t *>(&sm[0][0]);
+        static_assert(sizeof(sm) == TH * 8 * sizeof(uint32_t) && kBlockThreads == 2 * TH, "two draws per tile row");
+        const bool onebit = bit_draw(lat);
+        if (onebit) {
+            const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+            if (r < th) {
+                const uint32_t g0 = (uint32_t)(Y0 + r) * (uint32_t)L + (uint32_t)X0;
+                if (h == 0 || (g0 & 127u) + (uint32_t)tw > 128u)
+                    reinterpret_cast<uint4 *>(bits)[2 * r + h] = draw4(lat, (g0 >> 7) + (uint32_t)h, t, kTagStateBit);
+            }
+            __syncthreads();
+        }
         {
             const int nlab = s_nroots;
             for (int i = threadIdx.x; i < nlab; i += blockDim.x) {
@@ -868,8 +894,15 @@ __global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
                         w = kTileResolved | kCodeClosed;
                     }
                 } else {
-                    const uint32_t u = draw4(lat, (uint32_t)g, t, kTagState).x;
-                    w = kTileResolved | kCodeClosed | (clock ? (int)(u >> 31) : mulhi_q(u, q));
+                    int d;
+                    if (onebit) {   // bit g of the draws (draw_bit)
+                        const int r = v / TW;
+                        const uint32_t g0 = (uint32_t)(Y0 + r) * (uint32_t)L + (uint32_t)X0;
+                        d = (int)((bits[8 * r + ((uint32_t)g >> 5) - 4 * (g0 >> 7)] >> (g & 31)) & 1u);
+                    } else {
+                        d = mulhi_q(draw4(lat, (uint32_t)g, t, kTagState).x, q);
+                    }
+                    w = kTileResolved | kCodeClosed | d;
                     ++closed_roots;
                     if (lat.stats) atomicAdd(&s_nclosed, 1);
                 }
@@ -952,6 +985,7 @@ template <bool STATS>
 __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
 {
     static_assert(kMergeItems == TH + TW, "merge items: right edge rows, then bottom edge columns");
+    pdl_begin();
     long long lo = 0, hi = 0;
     int rep = -1;
     const Lattice *lp = b.lat;   // read through the L1, not copied into registers
@@ -1094,6 +1128,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
+    pdl_begin();
     const int r = threadIdx.x & 31;
     // q <= 8: state counts of this thread, 16 bits per state (states 0-3, 4-7);
     // q == 2: sites in cnt_hi, sites in state 1 in cnt_lo.
@@ -1200,8 +1235,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
                 const unsigned long long e = find_open(lat.opar, x, cap, lat.st, tl);
                 const uint32_t key = (uint32_t)(e >> 32);
                 if (MEASURE && (uint32_t)e == x) ++open_roots;
-                const uint32_t u = draw4(lat, key, ctx.t, kTagState).x;
-                tab[s] = clock ? (unsigned char)(u >> 31) : (unsigned char)mulhi_q(u, q);
+                tab[s] = (unsigned char)cluster_draw(lat, key, ctx.t);
                 if (LABELS) rootg[LABELS ? s : 0] = (int)key;
             }
         }
@@ -1416,12 +1450,33 @@ __global__ void k_count_invalid(const int8_t *spin, long long n, int q, unsigned
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
 }
 
+// One kernel of a sweep, with programmatic stream serialization (pdl_begin).
+template <typename K>
+cudaError_t launch_pdl(K kernel, int blocks, int threads, cudaStream_t s, const Batch &b)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, b);
+}
+
 template <bool MEASURE, bool LABELS>
 cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, cudaStream_t s, cudaEvent_t *ev)
 {
     int nev = 0;
     auto mark = [&]() {
         if (ev) cudaEventRecord(ev[nev++], s);
+    };
+    cudaError_t e = cudaSuccess;
+    auto put = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
     };
     mark();
     // Batches take the whole GPU's grid, whatever their current size, so that
@@ -1431,28 +1486,23 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
         return (int)std::max<long long>(1, b.full_grid ? cap : std::min(work, cap));
     };
     const int bblocks = grid(b.ntasks, shape.bonds);
-    if (b.any_clock)
-        k_bonds<MEASURE, true><<<bblocks, kBlockThreads, 0, s>>>(b);
-    else
-        k_bonds<MEASURE, false><<<bblocks, kBlockThreads, 0, s>>>(b);
+    put(launch_pdl(b.any_clock ? k_bonds<MEASURE, true> : k_bonds<MEASURE, false>, bblocks, kBlockThreads, s, b));
     mark();
-    k_label_tiles<MEASURE, LABELS><<<grid(b.ntasks, shape.label), kBlockThreads, 0, s>>>(b);
+    put(launch_pdl(k_label_tiles<MEASURE, LABELS>, grid(b.ntasks, shape.label), kBlockThreads, s, b));
     mark();
     const int mblocks = grid((b.nmerge + 255) / 256, shape.merge);
-    if (b.any_stats)
-        k_merge<true><<<mblocks, 256, 0, s>>>(b);
-    else
-        k_merge<false><<<mblocks, 256, 0, s>>>(b);
+    put(launch_pdl(b.any_stats ? k_merge<true> : k_merge<false>, mblocks, 256, s, b));
     mark();
     const int fblocks = grid(b.ntasks, std::min(shape.flip, b.any_clock ? kFlipResidentClock : kFlipResidentPotts));
     if (b.any_clock)
-        b.any_stats ? k_flip_tiles<MEASURE, LABELS, true, true><<<fblocks, kBlockThreads, 0, s>>>(b)
-                    : k_flip_tiles<MEASURE, LABELS, true, false><<<fblocks, kBlockThreads, 0, s>>>(b);
+        put(launch_pdl(b.any_stats ? k_flip_tiles<MEASURE, LABELS, true, true> : k_flip_tiles<MEASURE, LABELS, true, false>,
+                       fblocks, kBlockThreads, s, b));
     else
-        b.any_stats ? k_flip_tiles<MEASURE, LABELS, false, true><<<fblocks, kBlockThreads, 0, s>>>(b)
-                    : k_flip_tiles<MEASURE, LABELS, false, false><<<fblocks, kBlockThreads, 0, s>>>(b);
+        put(launch_pdl(b.any_stats ? k_flip_tiles<MEASURE, LABELS, false, true>
+                                   : k_flip_tiles<MEASURE, LABELS, false, false>,
+                       fblocks, kBlockThreads, s, b));
     mark();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace

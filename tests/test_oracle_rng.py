@@ -21,7 +21,7 @@ pytest.importorskip("triton")
 HERE = os.path.dirname(os.path.abspath(__file__))
 SEED = 0x9E3779B97F4A7C15
 T_NO_BONDS = 1e12          # p = 1 - exp(-1e-12) -> integer threshold 0
-TAG_BOND, TAG_STATE, TAG_AXIS, TAG_INIT = 0, 1, 2, 3
+TAG_BOND, TAG_STATE, TAG_AXIS, TAG_INIT, TAG_STATE_BIT = 0, 1, 2, 3, 4
 
 
 def _triton_philox(ctr, seed):
@@ -39,7 +39,7 @@ def table():
     idx = np.arange(1024, dtype=np.uint32)
     rows, keys = [], []
     for t in (0, 3):
-        for tag in range(4):
+        for tag in range(5):
             c = np.zeros((idx.size, 4), dtype=np.uint32)
             c[:, 0] = idx
             c[:, 1] = t
@@ -52,6 +52,13 @@ def table():
 
 def _mulhi(u, q):
     return ((u.astype(np.uint64) * np.uint64(q)) >> np.uint64(32)).astype(np.int64)
+
+
+def _bit(lanes, r):
+    """One-bit draws of roots r: bit r & 31 of lane (r >> 5) & 3 of the
+    STATE_BIT counter r >> 7."""
+    r = np.asarray(r, dtype=np.int64)
+    return ((lanes[r >> 7, (r >> 5) & 3] >> (r & 31).astype(np.uint32)) & 1).astype(np.int64)
 
 
 def test_philox_matches_triton_library():
@@ -76,14 +83,19 @@ def test_random_start_keying(table):
 
 @pytest.mark.parametrize("model,q", [(POTTS, 3), (ISING, 2), (POTTS, 2)])
 def test_no_bonds_every_site_draws_its_own_state(table, model, q):
-    """With p = 0 every site is a cluster of its own and takes
-    mulhi(u_STATE(site), q) -- Sec. 2 steps (v)-(vii)."""
+    """With p = 0 every site is a cluster of its own and takes a uniform
+    new state -- Sec. 2 steps (v)-(vii): mulhi(u_STATE(site), q) for q > 2,
+    the site's STATE_BIT bit for q = 2."""
     L = 32
     o = Oracle(L, q, model, T_NO_BONDS, SEED, init="random")
     assert o.thresholds()[0] == 0
     o.sweep_index = 3
     rec = o.sweep(1, record=True)[0]
-    want = _mulhi(table[(3, TAG_STATE)][: L * L, 0], q)
+    if q == 2:
+        want = _bit(table[(3, TAG_STATE_BIT)], np.arange(L * L))
+        assert 0.4 < want.mean() < 0.6
+    else:
+        want = _mulhi(table[(3, TAG_STATE)][: L * L, 0], q)
     assert np.array_equal(o.spins.reshape(-1), want)
     assert np.array_equal(o.labels.reshape(-1), np.arange(L * L))
     nclass = q // 2 + 1 if model == CLOCK else 2
@@ -130,7 +142,7 @@ def test_bond_lanes_labels_and_root_draws(table, L):
 
 def test_clock_axis_and_single_site_reflections(table):
     """Clock, p = 0: the sweep's axis is mulhi(u_AXIS(0, sweep), q); each site
-    is reflected k -> (m - k) mod q iff the top bit of its STATE draw is set."""
+    is reflected k -> (m - k) mod q iff its STATE_BIT bit is set."""
     q, L = 6, 32
     o = Oracle(L, q, CLOCK, T_NO_BONDS, SEED, init="random")
     assert int(o.thresholds().max()) == 0
@@ -139,7 +151,7 @@ def test_clock_axis_and_single_site_reflections(table):
     o.sweep(1)
     m = int(_mulhi(table[(3, TAG_AXIS)][0:1, 0], q)[0])
     assert o.axis == m
-    flip = (table[(3, TAG_STATE)][: L * L, 0] >> 31).astype(bool)
+    flip = _bit(table[(3, TAG_STATE_BIT)], np.arange(L * L)).astype(bool)
     want = np.where(flip, (m - before) % q, before)
     assert np.array_equal(o.spins.reshape(-1), want)
     o2 = Oracle(L, q, CLOCK, T_NO_BONDS, SEED, init="random")
