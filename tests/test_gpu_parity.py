@@ -166,6 +166,31 @@ def test_checkpoint_resume_is_bit_exact():
     c.close()
 
 
+@pytest.mark.parametrize("model,q,T", [(POTTS, 3, tc_potts(3)), (ISING, 2, TC_ISING), (CLOCK, 6, 0.9)])
+def test_spins_and_sweep_index_set_between_sweeps(model, q, T):
+    """Spins set between sweeps (the bond stage reads whatever spins it
+    finds) and a sweep index set between sweeps (it positions the random
+    stream) keep a captured chain equal to the oracle's."""
+    L = 100
+    g, o = make_pair(L, q, model, T, 31, "random")
+    sw.sw_set_graph(g.h, 1)
+    g.sweep(3)
+    o.sweep(3)
+    s = np.random.default_rng(5).integers(0, q, size=(L, L), dtype=np.int8)
+    g.spins = s
+    o.spins = s
+    g.sweep(2)
+    o.sweep(2)
+    assert np.array_equal(g.spins, o.spins), "after spins were set"
+    g.sweep_index = 40
+    o.sweep_index = 40
+    g.sweep(2)
+    o.sweep(2)
+    assert np.array_equal(g.spins, o.spins), "after the sweep index was set"
+    g.close()
+    o.close()
+
+
 def test_ring_drain_over_many_sweeps():
     """More sweeps than the device counter ring holds (drained mid-call)."""
     L, n = 16, 2600
