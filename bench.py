@@ -50,7 +50,11 @@ ALG_BYTES_PER_SITE = {"bonds": 1.25, "label": 2.25, "merge": None, "flip": 3.0}
 # materialised): spin read + label write + label read + spin write.
 SWEEP_BYTES_PER_SITE = 10.0
 NOMINAL_HBM_GBS = 8000.0   # the metric's own denominator (GB300 HBM3e, nominal)
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1202_0635_gb300", "csrc", "sw_kernels.cu")
+# The sources that define the sweep kernels (an ncu side record describes
+# the kernels built from exactly these).
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1202_0635_gb300", "csrc", f)
+                  for f in ("sw_kernels.cu", "sw_device.cuh", "sw_internal.h")]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 def log(*a):
@@ -174,10 +178,56 @@ def combine_ranks(total_ms, steps, n_sites, world, dist=None, device="cpu"):
 
 
 def kernel_source_sha256():
-    """Hash of the kernel source, to tell whether an ncu side record still
+    """Hash of the kernel sources, to tell whether an ncu side record still
     describes the kernels being timed."""
-    with open(KERNEL_SOURCE, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+# ncu's raw-page units (SI prefixes) -> multiplier.
+_NCU_SCALE = {"": 1.0, "K": 1e3, "M": 1e6, "G": 1e9, "T": 1e12}
+
+
+def record_ncu(csv_path, source, out=TRAFFIC_FILE):
+    """Write the side record bench.py's roofline uses from an ncu capture of
+    one sweep (`ncu -i <report> --page raw --csv`): per stage, the DRAM bytes
+    (read + write) and warp instructions of its first captured launch, with
+    the hash of the kernel sources they describe."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr, units, data = rows[0], rows[1], rows[2:]
+    col = {name: i for i, name in enumerate(hdr)}
+
+    def value(d, name, base):
+        u = units[col[name]]
+        prefix = u[: len(u) - len(base)] if u.endswith(base) else ""
+        return float(d[col[name]].replace(",", "")) * _NCU_SCALE.get(prefix, 1.0)
+
+    kernel_of = {"k_bonds": "bonds", "k_label_tiles": "label", "k_merge": "merge", "k_flip_tiles": "flip"}
+    rec = {"source": source, "kernel_source_sha256": kernel_source_sha256(), "warp_instructions": {},
+           "duration_us": {}}
+    for d in data:
+        name = d[col["Kernel Name"]]
+        stage = next((v for k, v in kernel_of.items() if k + "<" in name or name.endswith(k) or k + "(" in name),
+                     None)
+        if stage is None or stage in rec:
+            continue
+        rec[stage] = value(d, "dram__bytes_read.sum", "byte") + value(d, "dram__bytes_write.sum", "byte")
+        rec["warp_instructions"][stage] = value(d, "smsp__inst_executed.sum", "inst")
+        tu = units[col["gpu__time_duration.sum"]]
+        to_us = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3, "s": 1e6,
+                 "second": 1e6}[tu]
+        rec["duration_us"][stage] = float(d[col["gpu__time_duration.sum"]].replace(",", "")) * to_us
+    missing = [s for s in kernel_of.values() if s not in rec]
+    if missing:
+        raise SystemExit("no launch of %s in %s" % (", ".join(missing), csv_path))
+    with open(out, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
 
 
 def _oracle_sample(task):
@@ -375,7 +425,7 @@ def run_ours(args, world, rank, local):
     lat = sw.Lattice(L, Q_BENCH, sw.SW_POTTS, T_BENCH, 1 + rank, init=sw.SW_INIT_RANDOM,
                      stream=stream.cuda_stream)
     sw.sw_set_graph(lat.h, 1)
-    lat.sweep(EQUIL_SWEEPS)
+    lat.sweep(args.equil)
     sw.sw_reset_stats(lat.h)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -427,7 +477,7 @@ def run_ours(args, world, rank, local):
     # ncu side records (DRAM traffic, warp instructions per launch): used only
     # while the kernel source is the one they were captured from.
     traffic, winst, stale = None, None, None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    tfile = TRAFFIC_FILE
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
@@ -529,7 +579,7 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "q=2 Potts (Ising) L=4096 periodic, T=Tc=1/ln(1+sqrt2), random start + %d "
-                               "equilibration sweeps; one sweep per step, measurement on, CUDA graph" % EQUIL_SWEEPS,
+                               "equilibration sweeps; one sweep per step, measurement on, CUDA graph" % args.equil,
                    "L": L, "q": Q_BENCH, "T": T_BENCH, "l2": "flushed before every timed sweep (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single lattice"},
         "roofline": roofline,
@@ -561,7 +611,15 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--equil", type=int, default=EQUIL_SWEEPS,
+                    help="untimed equilibration sweeps before the warm-up (fewer for profiler captures)")
+    ap.add_argument("--record-ncu", metavar="CSV",
+                    help="write profiles/traffic.json from an ncu raw-page CSV of one sweep's kernels, then exit")
+    ap.add_argument("--record-source", default="", help="how the --record-ncu capture was made (stored with it)")
     args = ap.parse_args()
+    if args.record_ncu:
+        print(json.dumps(record_ncu(args.record_ncu, args.record_source)))
+        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     world, rank, local = dist_setup()
