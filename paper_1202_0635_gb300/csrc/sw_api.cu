@@ -61,6 +61,29 @@ uint32_t threshold_of(double x)
     return (uint32_t)scaled;
 }
 
+// Clock-model bond thresholds (Sec. 4 embedding, J = 1) of every pair of
+// projection classes a, b = (2k - m) mod 2q for the sweep's mirror axis m:
+// 1 - exp(-2 K s_a s_b), K = 1 / T, with s = sin(pi (j mod q) / q) when both
+// classes project strictly onto the same side of the axis, else 0; (2q)^2
+// entries, each rounded as (2 K) (s_a s_b) in double.
+std::vector<uint32_t> clock_thresholds(int q, double T)
+{
+    const double K = 1.0 / T;
+    const int n2 = 2 * q;
+    std::vector<uint32_t> tab((size_t)n2 * n2, 0u);
+    for (int a = 0; a < n2; ++a) {
+        for (int b = 0; b < n2; ++b) {
+            const int side_a = (a % q == 0) ? 0 : (a < q ? 1 : -1);
+            const int side_b = (b % q == 0) ? 0 : (b < q ? 1 : -1);
+            if (side_a == 0 || side_a != side_b) continue;
+            const double pa = std::sin((M_PI * (double)(a % q)) / (double)q);
+            const double pb = std::sin((M_PI * (double)(b % q)) / (double)q);
+            tab[(size_t)a * n2 + b] = threshold_of((2.0 * K) * (pa * pb));
+        }
+    }
+    return tab;
+}
+
 int nclass_of(int q, int model) { return model == SW_CLOCK ? q / 2 + 1 : 2; }
 
 // Counters per sweep: n_k, bond classes, active bonds, clusters; the clock
@@ -643,18 +666,7 @@ sw_handle *create_impl(int L, int q, int model, double T, uint64_t seed, void *d
     } else if (model == SW_ISING) {
         h->thr = threshold_of(2.0 * K);
     } else {
-        const int n2 = 2 * q;
-        h->thr_tab.assign((size_t)n2 * n2, 0u);
-        for (int a = 0; a < n2; ++a) {
-            for (int b = 0; b < n2; ++b) {
-                const int side_a = (a % q == 0) ? 0 : (a < q ? 1 : -1);
-                const int side_b = (b % q == 0) ? 0 : (b < q ? 1 : -1);
-                if (side_a == 0 || side_a != side_b) continue;
-                const double pa = std::sin((M_PI * (double)(a % q)) / (double)q);
-                const double pb = std::sin((M_PI * (double)(b % q)) / (double)q);
-                h->thr_tab[(size_t)a * n2 + b] = threshold_of((2.0 * K) * (pa * pb));
-            }
-        }
+        h->thr_tab = clock_thresholds(q, T);
         if ((e = cudaMalloc(&h->d_thr_tab, h->thr_tab.size() * sizeof(uint32_t))) != cudaSuccess)
             return bail(e, "cudaMalloc(thresholds)");
         if ((e = cudaMemcpy(h->d_thr_tab, h->thr_tab.data(), h->thr_tab.size() * sizeof(uint32_t),
@@ -1616,18 +1628,7 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     } else if (model == SW_ISING) {
         lat.thr = threshold_of(2.0 / T);
     } else {
-        const int n2 = 2 * q;
-        tab.assign((size_t)n2 * n2, 0u);
-        for (int a = 0; a < n2; ++a) {
-            for (int b = 0; b < n2; ++b) {
-                const int side_a = (a % q == 0) ? 0 : (a < q ? 1 : -1);
-                const int side_b = (b % q == 0) ? 0 : (b < q ? 1 : -1);
-                if (side_a == 0 || side_a != side_b) continue;
-                const double pa = std::sin((M_PI * (double)(a % q)) / (double)q);
-                const double pb = std::sin((M_PI * (double)(b % q)) / (double)q);
-                tab[(size_t)a * n2 + b] = threshold_of((2.0 / T) * (pa * pb));
-            }
-        }
+        tab = clock_thresholds(q, T);
         lat.thr_tab = (const uint32_t *)(base + kNoalloc.thr_tab);
     }
     const int task_off[2] = {0, tiles_x * tiles_y};

@@ -43,6 +43,8 @@ constexpr unsigned FULL = 0xffffffffu;
 // Resident blocks per SM of the flip kernel's variants (its launch bounds);
 // its grid never asks for more, so that one wave covers the tiles.
 constexpr int kFlipResidentPotts = 10, kFlipResidentClock = 8;
+// Resident blocks per SM of the labeling kernel that draws the bonds itself.
+constexpr int kLabelResidentFused = 10;
 // Resolved root word: kTileResolved | the cluster's per-site code, i.e.
 // kCodeClosed | new state (Potts) or reflection flag (clock), or the open
 // slot.
@@ -361,6 +363,75 @@ __device__ __forceinline__ void clock_row_classes(unsigned int *hist_class, unsi
 // ANY_CLOCK: the batch holds a clock lattice; the clock code is compiled in.
 // The bounds keep the clock measuring variant at 80 registers and the
 // Potts-only variants at 8 resident blocks per SM, without spills.
+// The states of the half row (y, x0 .. x0 + ncols - 1) and of the half row
+// below it (periodic), four to a word, and the right neighbour of its last
+// site.  Nothing is loaded unless rv (then all are 0).
+__device__ __forceinline__ void load_half_rows(const int8_t *spin, int L, int y, int x0, int ncols, bool rv,
+                                               uint32_t (&wd)[8], uint32_t (&dn)[8], uint32_t &sr)
+{
+    const size_t rowbase = (size_t)y * L + x0;
+    const int yd = (y + 1 == L) ? 0 : y + 1;
+    const uint32_t *row = reinterpret_cast<const uint32_t *>(spin + rowbase);
+    const uint32_t *drow = reinterpret_cast<const uint32_t *>(spin + (size_t)yd * L + x0);
+    if ((L & 15) == 0 && ncols == QW) {   // whole half row, 16-byte aligned
+        const uint4 a0 = rv ? __ldg(reinterpret_cast<const uint4 *>(row)) : make_uint4(0, 0, 0, 0);
+        const uint4 a1 = rv ? __ldg(reinterpret_cast<const uint4 *>(row) + 1) : make_uint4(0, 0, 0, 0);
+        const uint4 b0 = rv ? __ldg(reinterpret_cast<const uint4 *>(drow)) : make_uint4(0, 0, 0, 0);
+        const uint4 b1 = rv ? __ldg(reinterpret_cast<const uint4 *>(drow) + 1) : make_uint4(0, 0, 0, 0);
+        wd[0] = a0.x; wd[1] = a0.y; wd[2] = a0.z; wd[3] = a0.w;
+        wd[4] = a1.x; wd[5] = a1.y; wd[6] = a1.z; wd[7] = a1.w;
+        dn[0] = b0.x; dn[1] = b0.y; dn[2] = b0.z; dn[3] = b0.w;
+        dn[4] = b1.x; dn[5] = b1.y; dn[6] = b1.z; dn[7] = b1.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool ok = rv && 4 * k < ncols;
+            wd[k] = ok ? __ldg(row + k) : 0u;
+            dn[k] = ok ? __ldg(drow + k) : 0u;
+        }
+    }
+    sr = 0;
+    if (rv) {
+        const int xr = (x0 + ncols == L) ? 0 : x0 + ncols;
+        sr = (uint8_t)__ldg(spin + (size_t)y * L + xr);
+    }
+}
+
+// Potts bonds of a half row (Sec. 2 step (ii)) from its states (wd, dn,
+// sr as load_half_rows gives them): bit c of R / D is the bond from site c
+// to its right / lower neighbour, set iff the two states are equal and the
+// bond's lane of the site pair's BOND draw lies below the threshold.  eqR /
+// eqD: the equal-neighbour masks.  rowbase: index of the half row's first
+// site (even).
+__device__ __forceinline__ void potts_bonds(const Lattice &lat, unsigned long long t, size_t rowbase, int ncols,
+                                            bool rv, const uint32_t (&wd)[8], const uint32_t (&dn)[8], uint32_t sr,
+                                            unsigned &R, unsigned &D, unsigned &eqR, unsigned &eqD)
+{
+    const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
+    eqR = eqD = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
+        eqR |= zero_bytes4(wd[k] ^ __funnelshift_r(wd[k], nxt, 8)) << (4 * k);
+        eqD |= zero_bytes4(wd[k] ^ dn[k]) << (4 * k);
+    }
+    unsigned rR = 0u, rD = 0u;
+    if (rv) {
+        const uint32_t pbase = (uint32_t)(rowbase >> 1);
+        const uint32_t thr = lat.thr;
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            if (2 * p < ncols) {
+                const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
+                rR |= ((unsigned)(u.x < thr) << (2 * p)) | ((unsigned)(u.z < thr) << (2 * p + 1));
+                rD |= ((unsigned)(u.y < thr) << (2 * p)) | ((unsigned)(u.w < thr) << (2 * p + 1));
+            }
+        }
+    }
+    R = rv ? (rR & eqR & V) : 0u;
+    D = rv ? (rD & eqD & V) : 0u;
+}
+
 template <bool MEASURE, bool ANY_CLOCK>
 __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) : 8) k_bonds(Batch b)
 {
@@ -433,7 +504,6 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
         const bool clock = ANY_CLOCK && lat.clock != 0;
         if (!ANY_CLOCK && lat.clock && threadIdx.x == 0) record_error(lat.st, kErrInternal, 0);   // wrong variant
         const unsigned long long t = ctx.t;
-        const uint32_t thr = lat.thr;
         // Clock bond threshold of valid states a, b.
         auto cthr = [&](int a, int c) -> uint32_t { return s_thr[a * q + c]; };
         const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
@@ -444,34 +514,9 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
         const int ncols = max(0, min(QW, tw - QW * hx));
         const bool rv = ry < th && ncols > 0;
         const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
-        uint32_t wd[8], dn[8], sr = 0;
+        uint32_t wd[8], dn[8], sr;
         const size_t rowbase = (size_t)y * L + x0;   // meaningful only if rv
-        {
-            const int yd = (y + 1 == L) ? 0 : y + 1;
-            const uint32_t *row = reinterpret_cast<const uint32_t *>(lat.spin + rowbase);
-            const uint32_t *drow = reinterpret_cast<const uint32_t *>(lat.spin + (size_t)yd * L + x0);
-            if ((L & 15) == 0 && ncols == QW) {   // whole half row, 16-byte aligned
-                const uint4 a0 = rv ? __ldg(reinterpret_cast<const uint4 *>(row)) : make_uint4(0, 0, 0, 0);
-                const uint4 a1 = rv ? __ldg(reinterpret_cast<const uint4 *>(row) + 1) : make_uint4(0, 0, 0, 0);
-                const uint4 b0 = rv ? __ldg(reinterpret_cast<const uint4 *>(drow)) : make_uint4(0, 0, 0, 0);
-                const uint4 b1 = rv ? __ldg(reinterpret_cast<const uint4 *>(drow) + 1) : make_uint4(0, 0, 0, 0);
-                wd[0] = a0.x; wd[1] = a0.y; wd[2] = a0.z; wd[3] = a0.w;
-                wd[4] = a1.x; wd[5] = a1.y; wd[6] = a1.z; wd[7] = a1.w;
-                dn[0] = b0.x; dn[1] = b0.y; dn[2] = b0.z; dn[3] = b0.w;
-                dn[4] = b1.x; dn[5] = b1.y; dn[6] = b1.z; dn[7] = b1.w;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const bool ok = rv && 4 * k < ncols;
-                    wd[k] = ok ? __ldg(row + k) : 0u;
-                    dn[k] = ok ? __ldg(drow + k) : 0u;
-                }
-            }
-            if (rv) {
-                const int xr = (x0 + ncols == L) ? 0 : x0 + ncols;
-                sr = (uint8_t)__ldg(lat.spin + (size_t)y * L + xr);
-            }
-        }
+        load_half_rows(lat.spin, L, y, x0, ncols, rv, wd, dn, sr);
         if (clock) {   // states outside [0, q) read as 0: they index the q x q threshold table
             const uint32_t q4 = (uint32_t)q * 0x01010101u;
 #pragma unroll
@@ -481,27 +526,13 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
             }
             sr = (uint32_t)valid_state((int)sr, q);
         }
-        unsigned eqR = 0, eqD = 0, rR = 0, rD = 0;
+        unsigned eqR = 0, eqD = 0, R = 0, D = 0;
         if (!clock) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
-                eqR |= zero_bytes4(wd[k] ^ __funnelshift_r(wd[k], nxt, 8)) << (4 * k);
-                eqD |= zero_bytes4(wd[k] ^ dn[k]) << (4 * k);
-            }
-        }
-        if (rv) {
+            potts_bonds(lat, t, rowbase, ncols, rv, wd, dn, sr, R, D, eqR, eqD);
+        } else if (rv) {
+            unsigned rR = 0, rD = 0;
             const uint32_t pbase = (uint32_t)(rowbase >> 1);
-            if (!clock) {
-#pragma unroll
-                for (int p = 0; p < 16; ++p) {
-                    if (2 * p < ncols) {
-                        const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
-                        rR |= ((unsigned)(u.x < thr) << (2 * p)) | ((unsigned)(u.z < thr) << (2 * p + 1));
-                        rD |= ((unsigned)(u.y < thr) << (2 * p)) | ((unsigned)(u.w < thr) << (2 * p + 1));
-                    }
-                }
-            } else {
+            {
 #pragma unroll
                 for (int p = 0; p < 16; ++p) {
                     if (2 * p < ncols) {
@@ -515,9 +546,9 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
                     }
                 }
             }
+            R = rR & V;
+            D = rD & V;
         }
-        const unsigned R = rv ? (clock ? (rR & V) : (rR & eqR & V)) : 0u;
-        const unsigned D = rv ? (clock ? (rD & V) : (rD & eqD & V)) : 0u;
         if (MEASURE) {
             active += __popc(R) + __popc(D);
             if (ctx.count_classes) {
@@ -627,8 +658,11 @@ struct RowMasks {
 //            open slot; the open slots of the right and left edge sites go
 //            to the tile's edge bytes.
 // ---------------------------------------------------------------------------
-template <bool MEASURE, bool LABELS>
-__global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
+// FUSED (batches without a clock lattice): the bonds are drawn here, each
+// thread its half row (as k_bonds does), instead of read from the bond
+// masks; the Philox work then fills the issue slots the labeling leaves.
+template <bool MEASURE, bool LABELS, bool FUSED>
+__global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 11) k_label_tiles(Batch b)
 {
     // Node words: provisional label of every node, which for a label's own
     // first node is its union-find parent.
@@ -652,12 +686,23 @@ __global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
     const int row = QW * qy + lane;   // my tile row (lane = row phases)
 
     unsigned int closed_roots = 0;
+    unsigned int active = 0, unequal = 0, pairs = 0;   // FUSED: k_bonds' counters
     int cur = -1;
     if (threadIdx.x < kCrossWords) s_cross[threadIdx.x] = 0u;   // before the first barrier below
-    // Counters of lattice `cur` -> its ring row (whole block).
+    // Counters of lattice `cur` -> its ring rows (whole block).
     auto flush = [&]() {
-        if (MEASURE && cur >= 0) block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass + 1, closed_roots, red);
-        closed_roots = 0;
+        if (MEASURE && cur >= 0) {
+            block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass + 1, closed_roots, red);
+            if (FUSED) {
+                block_add<kBlockThreads>(ring_row(lat, ctx.t) + lat.q + lat.nclass, active, red);
+                if (ctx.count_classes) {
+                    unsigned long long *prev = ring_row(lat, ctx.t - 1);
+                    block_add<kBlockThreads>(prev + lat.q + 1, unequal, red);
+                    block_add<kBlockThreads>(prev + lat.q + 0, pairs - unequal, red);
+                }
+            }
+        }
+        closed_roots = active = unequal = pairs = 0;
         __syncthreads();
     };
 
@@ -689,13 +734,30 @@ __global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
         const int cap = lat.dbg_loop_cap > 0 ? lat.dbg_loop_cap : NS + 1;   // loop bound
         const int ulist = lat.dbg_list_cap > 0 ? min(kUnionList, lat.dbg_list_cap) : kUnionList;
 
-        // ===== masks (lane = row; bond masks written by k_bonds) ================
+        // ===== masks (lane = row; bond masks written by k_bonds or drawn here) ====
         unsigned S = 0u, U2 = 0u;
         bool seam = false;
         {
-            const uint32_t *tb = lat.bond + (size_t)tile * kBondWords + row * 2 + qx;
-            const unsigned R = rv ? __ldg(tb) : 0u;
-            const unsigned D = rv ? __ldg(tb + kBlockThreads) : 0u;
+            unsigned R, D;
+            if (FUSED) {
+                if (lat.clock && threadIdx.x == 0) record_error(lat.st, kErrInternal, 0);   // wrong variant
+                const int y = Y0 + row, x0 = X0 + QW * qx;
+                uint32_t wd[8], dn[8], sr;
+                load_half_rows(lat.spin, L, y, x0, ncols, rv, wd, dn, sr);
+                unsigned eqR, eqD;
+                potts_bonds(lat, t, (size_t)y * L + x0, ncols, rv, wd, dn, sr, R, D, eqR, eqD);
+                if (MEASURE) {
+                    active += __popc(R) + __popc(D);
+                    if (ctx.count_classes && rv) {
+                        unequal += __popc(~eqR & V) + __popc(~eqD & V);
+                        pairs += 2u * (unsigned)ncols;
+                    }
+                }
+            } else {
+                const uint32_t *tb = lat.bond + (size_t)tile * kBondWords + row * 2 + qx;
+                R = rv ? __ldg(tb) : 0u;
+                D = rv ? __ldg(tb + kBlockThreads) : 0u;
+            }
             if (qa) {
                 const unsigned rc_bits = __ballot_sync(FULL, rv && ((R >> (ncols - 1)) & 1u));   // leaving the right edge
                 const unsigned dc_bits = __shfl_sync(FULL, D, nrows - 1) & V;                   // leaving the bottom edge
@@ -792,13 +854,16 @@ __global__ void __launch_bounds__(kBlockThreads, 11) k_label_tiles(Batch b)
         }
         __syncthreads();
         {
+            // Each thread joins a contiguous run of the list: pairs listed
+            // together (neighbouring rows of one quadrant) often share a
+            // component, and run one after the other instead of contending
+            // for its root at once.
             const int np = min(s_npairs, ulist);
-            for (int i0 = 0; i0 < np; i0 += blockDim.x) {   // uniform trip count: warp-wide dedup
-                const int i = i0 + threadIdx.x;
-                const uint32_t pr = i < np ? upairs[i] : 0u;
-                const unsigned peers = __match_any_sync(FULL, pr);
-                if (pr != 0u && (__ffs(peers) - 1) == lane &&
-                    !union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), cap))
+            const int per = (np + (int)blockDim.x - 1) / (int)blockDim.x;
+            const int i1 = min(np, ((int)threadIdx.x + 1) * per);
+            for (int i = (int)threadIdx.x * per; i < i1; ++i) {
+                const uint32_t pr = upairs[i];
+                if (pr != 0u && !union_t(X, (int)(pr & 0xFFFFu), (int)(pr >> 16), cap))
                     record_error(lat.st, kErrUnionCap, Y0 * L + X0);
             }
         }
@@ -1485,10 +1550,15 @@ cudaError_t sweep_impl(const Batch &b, int sm_count, const LaunchShape &shape, c
         const long long cap = (long long)sm_count * per_sm;
         return (int)std::max<long long>(1, b.full_grid ? cap : std::min(work, cap));
     };
-    const int bblocks = grid(b.ntasks, shape.bonds);
-    put(launch_pdl(b.any_clock ? k_bonds<MEASURE, true> : k_bonds<MEASURE, false>, bblocks, kBlockThreads, s, b));
-    mark();
-    put(launch_pdl(k_label_tiles<MEASURE, LABELS>, grid(b.ntasks, shape.label), kBlockThreads, s, b));
+    if (b.any_clock) {   // bonds in their own kernel (the clock threshold table), then the labeling
+        put(launch_pdl(k_bonds<MEASURE, true>, grid(b.ntasks, shape.bonds), kBlockThreads, s, b));
+        mark();
+        put(launch_pdl(k_label_tiles<MEASURE, LABELS, false>, grid(b.ntasks, shape.label), kBlockThreads, s, b));
+    } else {             // bonds drawn by the labeling kernel
+        mark();
+        put(launch_pdl(k_label_tiles<MEASURE, LABELS, true>, grid(b.ntasks, std::min(shape.label, kLabelResidentFused)),
+                       kBlockThreads, s, b));
+    }
     mark();
     const int mblocks = grid((b.nmerge + 255) / 256, shape.merge);
     put(launch_pdl(b.any_stats ? k_merge<true> : k_merge<false>, mblocks, 256, s, b));
