@@ -185,11 +185,18 @@ __device__ __forceinline__ void record_error(DevState *st, int code, int where)
 // low word, so entries order by key.  A root is its own parent.  Roots are
 // linked larger key under smaller with a 64-bit atomicMin, so the root of a
 // tree is its component with the smallest site; path halving writes only
-// ancestors.
+// ancestors.  Entries are read through the L1 (a load the compiler keeps):
+// a stale entry names an older ancestor, which is still an ancestor since
+// links only join roots; a root the walk takes for one is checked by the
+// link's atomicMin, which hands back the current parent to retry with; and
+// while the flip stage walks, no entry of a root changes -- so the many
+// walks that end at one large cluster's root mostly hit the L1.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long *p)
+__device__ __forceinline__ unsigned long long ld_entry(const unsigned long long *p)
 {
-    return *reinterpret_cast<const volatile unsigned long long *>(p);
+    unsigned long long v;
+    asm volatile("ld.global.ca.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 // Tallies of the global union-find (labeling statistics).
@@ -205,14 +212,14 @@ __device__ __forceinline__ unsigned long long find_open(unsigned long long *par,
     ++tl.finds;
     unsigned int steps = 0;
     for (int it = 0; it < cap; ++it) {
-        const unsigned long long e = ld_volatile64(par + x);
+        const unsigned long long e = ld_entry(par + x);
         const uint32_t p = (uint32_t)e;
         if (p == x) {
             tl.hops += steps;
             tl.max_hops = max(tl.max_hops, steps);
             return e;
         }
-        const unsigned long long ep = ld_volatile64(par + p);
+        const unsigned long long ep = ld_entry(par + p);
         const uint32_t gp = (uint32_t)ep;
         ++steps;
         if (gp == p) {
@@ -225,11 +232,11 @@ __device__ __forceinline__ unsigned long long find_open(unsigned long long *par,
         x = gp;
         if ((it & 255) == 255 && clock64() - t0 > kLoopBudgetCycles) {
             record_error(st, kErrTimeBudget, (int)x);
-            return ld_volatile64(par + x);
+            return ld_entry(par + x);
         }
     }
     record_error(st, kErrFindCap, (int)x);
-    return ld_volatile64(par + x);
+    return ld_entry(par + x);
 }
 
 __device__ __forceinline__ void union_open(unsigned long long *par, uint32_t a, uint32_t b, int cap, DevState *st,
@@ -237,7 +244,7 @@ __device__ __forceinline__ void union_open(unsigned long long *par, uint32_t a, 
 {
     const long long t0 = clock64();
     // Both entries in flight at once: most ends are roots already.
-    unsigned long long ea = ld_volatile64(par + a), eb = ld_volatile64(par + b);
+    unsigned long long ea = ld_entry(par + a), eb = ld_entry(par + b);
     if ((uint32_t)ea != a) ea = find_open(par, a, cap, st, tl);
     if ((uint32_t)eb != b) eb = find_open(par, b, cap, st, tl);
     for (int it = 0; it < cap; ++it) {

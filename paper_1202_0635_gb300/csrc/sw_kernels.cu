@@ -43,8 +43,9 @@ constexpr unsigned FULL = 0xffffffffu;
 // Resident blocks per SM of the flip kernel's variants (its launch bounds);
 // its grid never asks for more, so that one wave covers the tiles.
 constexpr int kFlipResidentPotts = 10, kFlipResidentClock = 8;
-// Resident blocks per SM of the labeling kernel that draws the bonds itself.
-constexpr int kLabelResidentFused = 10;
+// Resident blocks per SM of the labeling kernel that draws the bonds itself,
+// and the bond draws its threads keep in flight.
+constexpr int kLabelResidentFused = 11, kFusedDrawUnroll = 16;
 // Resolved root word: kTileResolved | the cluster's per-site code, i.e.
 // kCodeClosed | new state (Potts) or reflection flag (clock), or the open
 // slot.
@@ -134,13 +135,16 @@ __device__ __forceinline__ void add_hist_any(unsigned int *hist, int v, bool val
 }
 
 // The kernels of a sweep are launched with programmatic stream
-// serialization: the next kernel of the stream launches as this one's
-// blocks exit, and waits here until the previous kernel has completed and
-// its writes are visible.  Nothing before this point touches memory.
-// (Launched without the attribute, the wait does nothing.)
+// serialization: each waits here until the previous kernel has completed and
+// its writes are visible (nothing before this point touches memory), then
+// lets the next kernel of the stream launch, so that its blocks take the
+// SMs this kernel's last blocks leave and wait there instead of being
+// launched after the grid drains.  (Launched without the attribute, both
+// do nothing.)
 __device__ __forceinline__ void pdl_begin()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Per-lattice values every block needs once per task.
@@ -402,7 +406,8 @@ __device__ __forceinline__ void load_half_rows(const int8_t *spin, int L, int y,
 // to its right / lower neighbour, set iff the two states are equal and the
 // bond's lane of the site pair's BOND draw lies below the threshold.  eqR /
 // eqD: the equal-neighbour masks.  rowbase: index of the half row's first
-// site (even).
+// site (even).  UNROLL: draws in flight per thread (registers vs overlap).
+template <int UNROLL>
 __device__ __forceinline__ void potts_bonds(const Lattice &lat, unsigned long long t, size_t rowbase, int ncols,
                                             bool rv, const uint32_t (&wd)[8], const uint32_t (&dn)[8], uint32_t sr,
                                             unsigned &R, unsigned &D, unsigned &eqR, unsigned &eqD)
@@ -419,7 +424,7 @@ __device__ __forceinline__ void potts_bonds(const Lattice &lat, unsigned long lo
     if (rv) {
         const uint32_t pbase = (uint32_t)(rowbase >> 1);
         const uint32_t thr = lat.thr;
-#pragma unroll
+#pragma unroll UNROLL
         for (int p = 0; p < 16; ++p) {
             if (2 * p < ncols) {
                 const uint4 u = draw4(lat, pbase + (uint32_t)p, t, kTagBond);
@@ -528,7 +533,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) :
         }
         unsigned eqR = 0, eqD = 0, R = 0, D = 0;
         if (!clock) {
-            potts_bonds(lat, t, rowbase, ncols, rv, wd, dn, sr, R, D, eqR, eqD);
+            potts_bonds<16>(lat, t, rowbase, ncols, rv, wd, dn, sr, R, D, eqR, eqD);
         } else if (rv) {
             unsigned rR = 0, rD = 0;
             const uint32_t pbase = (uint32_t)(rowbase >> 1);
@@ -745,7 +750,7 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
                 uint32_t wd[8], dn[8], sr;
                 load_half_rows(lat.spin, L, y, x0, ncols, rv, wd, dn, sr);
                 unsigned eqR, eqD;
-                potts_bonds(lat, t, (size_t)y * L + x0, ncols, rv, wd, dn, sr, R, D, eqR, eqD);
+                potts_bonds<kFusedDrawUnroll>(lat, t, (size_t)y * L + x0, ncols, rv, wd, dn, sr, R, D, eqR, eqD);
                 if (MEASURE) {
                     active += __popc(R) + __popc(D);
                     if (ctx.count_classes && rv) {
