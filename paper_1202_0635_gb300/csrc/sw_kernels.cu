@@ -1,18 +1,20 @@
 // sw_kernels.cu -- the kernels of one Swendsen-Wang sweep on sm_103a.
 //
 // One sweep (Komura & Okabe, arXiv:1202.0635, Sec. 2 steps (i)-(viii);
-// clock model: Sec. 4 embedded clusters) is four launches over the 64 x 64
-// tiles of every lattice of a batch (a single lattice is a batch of one).
-// A block owns one tile of one lattice at a time ("task"), so per-lattice
-// counters reduce per block.
+// clock model: Sec. 4 embedded clusters) is three launches over the 64 x 64
+// tiles of every lattice of a batch (a single lattice is a batch of one),
+// four when the batch holds a clock lattice.  A block owns one tile of one
+// lattice at a time ("task"), so per-lattice counters reduce per block.
 //
-//   k_bonds        bonds of every site (Sec. 2 (ii)): equal-neighbour masks
-//                  from packed byte compares, Philox draws against the
-//                  integer threshold; the masks go to a per-tile buffer.
-//                  With measurement on it also counts the bond classes of
-//                  the incoming configuration (the previous sweep's result)
-//                  and the active bonds.
-//   k_label_tiles  tile-local clusters by a row-by-row labeling with a
+//   k_bonds        (batches with a clock lattice) bonds of every site
+//                  (Sec. 2 (ii); Sec. 4): Philox draws against the integer
+//                  threshold of the state pair; the masks go to a per-tile
+//                  buffer.  With measurement on it also counts the bond
+//                  classes of the incoming configuration (the previous
+//                  sweep's result) and the active bonds.
+//   k_label_tiles  (Potts batches: first the bonds of the tile, as k_bonds
+//                  draws them, from packed byte compares of the states)
+//                  tile-local clusters by a row-by-row labeling with a
 //                  union-find in shared memory (four warps, one 32 x 32
 //                  quadrant each).  A component that does not reach the tile
 //                  border (or reaches it only through inactive crossing bonds
@@ -354,19 +356,6 @@ __device__ __forceinline__ void clock_row_classes(unsigned int *hist_class, unsi
     }
 }
 
-// ---------------------------------------------------------------------------
-// k_bonds: the bonds of every site (Sec. 2 step (ii); clock: Sec. 4).
-// Thread = one 32-site half row of a tile: equal-neighbour masks from packed
-// byte compares, one Philox draw per two sites against the integer
-// threshold.  The masks of a tile are stored together (right bonds of its 64
-// rows, two words a row, then the down bonds), including the bonds that
-// cross into the next tile.  With measurement on it also counts the active
-// bonds and the bond classes of the incoming configuration (the previous
-// sweep's result).
-// ---------------------------------------------------------------------------
-// ANY_CLOCK: the batch holds a clock lattice; the clock code is compiled in.
-// The bounds keep the clock measuring variant at 80 registers and the
-// Potts-only variants at 8 resident blocks per SM, without spills.
 // The states of the half row (y, x0 .. x0 + ncols - 1) and of the half row
 // below it (periodic), four to a word, and the right neighbour of its last
 // site.  Nothing is loaded unless rv (then all are 0).
@@ -437,6 +426,20 @@ __device__ __forceinline__ void potts_bonds(const Lattice &lat, unsigned long lo
     D = rv ? (rD & eqD & V) : 0u;
 }
 
+// ---------------------------------------------------------------------------
+// k_bonds: the bonds of every site (Sec. 2 step (ii); clock: Sec. 4).
+// Thread = one 32-site half row of a tile: equal-neighbour masks from packed
+// byte compares, one Philox draw per two sites against the integer
+// threshold.  The masks of a tile are stored together (right bonds of its 64
+// rows, two words a row, then the down bonds), including the bonds that
+// cross into the next tile.  With measurement on it also counts the active
+// bonds and the bond classes of the incoming configuration (the previous
+// sweep's result).
+// ---------------------------------------------------------------------------
+// ANY_CLOCK: the batch holds a clock lattice; the clock code is compiled in
+// (the launches of a sweep use only this variant: Potts-only batches draw
+// their bonds in the labeling kernel).  The bounds keep the clock measuring
+// variant at 80 registers.
 template <bool MEASURE, bool ANY_CLOCK>
 __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? (MEASURE ? 6 : 1) : 8) k_bonds(Batch b)
 {
