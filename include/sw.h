@@ -332,8 +332,7 @@ int sw_batch_set_launch_shape(sw_batch *b, const int *shape);
  * Limits: 4 <= L <= SW_NOALLOC_MAX_L with L % 4 == 0, and the q / model / T
  * rules of sw_create; anything else returns SW_ERR_ARG before any GPU work.
  * The call returns once its work on `stream` is complete (it synchronises
- * the stream, also on an error after work was enqueued), so it cannot be
- * recorded into a CUDA graph by stream capture.
+ * the stream, also on an error after work was enqueued).
  *
  * The first call on a device looks up the array's device address (and may
  * load the library's device code onto that device); make that first call
