@@ -191,14 +191,17 @@ int sw_set_sweep(sw_handle *h, uint64_t t);
 int sw_set_sweep_limit(sw_handle *h, uint64_t stop);
 int sw_get_sweep_limit(sw_handle *h, uint64_t *out);
 
-/* Launch shape: resident blocks per SM requested for the four kernels of
- * a sweep, shape[4] = {labeling, merge, flip, bonds}, each in [1, 64]
- * (default {8, 16, 10, 16}; the flip grid never exceeds the blocks its
- * kernel keeps resident, 10 per SM, 8 with a clock lattice).
+/* Launch shape: resident blocks per SM requested for the kernels of a
+ * sweep, shape[4] = {labeling, merge, flip, bonds}, each in [1, 64]
+ * (default {11, 16, 10, 16}).  The labeling kernel that draws the bonds
+ * itself (batches without a clock lattice) keeps at most 11 blocks per SM,
+ * the flip kernel 10 (8 with a clock lattice); the bond figure applies only
+ * where the bond kernel runs (a clock lattice in the batch).
  * Results never depend on it.  sw_autotune times every candidate (n real
  * sweeps each, they advance the chain like any others), keeps the fastest
- * per kernel, caches it per (device, work size) for the process, and writes
- * the choice to shape_out (may be NULL).  A cached choice costs no sweeps. */
+ * per kernel, caches it per (device, work size, measurement, clock lattice)
+ * for the process, and writes the choice to shape_out (may be NULL).  A
+ * cached choice costs no sweeps. */
 int sw_autotune(sw_handle *h, int n, int *shape_out);
 int sw_set_launch_shape(sw_handle *h, const int *shape);
 

@@ -486,28 +486,29 @@ int timed_sweeps(const Batch &b, bool measure, bool labels, int sm_count, const 
 std::mutex g_tune_mu;
 std::map<std::string, LaunchShape> g_tune_cache;
 
-std::string tune_key(int nrep, int ntasks, long long nmerge, bool measure)
+std::string tune_key(int nrep, int ntasks, long long nmerge, bool measure, bool any_clock)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, dev);
     char buf[384];
-    snprintf(buf, sizeof buf, "%s|%d|%d|%lld|%d", prop.name, nrep, ntasks, nmerge, (int)measure);
+    snprintf(buf, sizeof buf, "%s|%d|%d|%lld|%d|%d", prop.name, nrep, ntasks, nmerge, (int)measure, (int)any_clock);
     return buf;
 }
 
 // Coordinate descent over the blocks per SM of each kernel: every
-// candidate runs n timed sweeps (real sweeps of the chain).
+// candidate runs n timed sweeps (real sweeps of the chain).  The bond
+// kernel's figure is tuned only where the sweep launches it (a clock lattice).
 template <typename Timer>
-int autotune_shape(LaunchShape *best, int n, Timer timer)
+int autotune_shape(LaunchShape *best, int n, bool tune_bonds, Timer timer)
 {
     static const int cand_label[] = {7, 9, 11};
     static const int cand_other[] = {4, 8, 16, 32};
     double ms[swgb::kMaxStages];
     // Timed stages: 0 bonds, 1 labeling, 2 merge, 3 flip.
     static const int stage_of[4] = {1, 2, 3, 0};   // tuned in the order label, merge, flip, bonds
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < (tune_bonds ? 4 : 3); ++k) {
         const int *cand = k == 0 ? cand_label : cand_other;
         const int ncand = k == 0 ? 3 : 4;
         double best_ms = 1e30;
@@ -989,7 +990,7 @@ int sw_autotune(sw_handle *h, int n, int *shape_out)
     if (n < 1) return fail(SW_ERR_ARG, "n must be positive");
     int rc = drain(h);
     if (rc != SW_OK) return rc;
-    const std::string key = tune_key(1, h->ntasks(), h->nmerge(), h->measure);
+    const std::string key = tune_key(1, h->ntasks(), h->nmerge(), h->measure, h->model == SW_CLOCK);
     LaunchShape best;
     bool cached = false;
     {
@@ -1001,7 +1002,7 @@ int sw_autotune(sw_handle *h, int n, int *shape_out)
         }
     }
     if (!cached) {
-        rc = autotune_shape(&best, n, [&](const LaunchShape &trial, int nn, double *ms) {
+        rc = autotune_shape(&best, n, h->model == SW_CLOCK, [&](const LaunchShape &trial, int nn, double *ms) {
             return timed_sweeps(
                 h->self_batch(), h->measure, h->labels, h->sm_count, trial, h->stream, nn, ms,
                 [&]() -> int {
@@ -1449,7 +1450,7 @@ int sw_batch_autotune(sw_batch *b, int n, int *shape_out)
         int rc = rebuild_batch(b);
         if (rc != SW_OK) return rc;
     }
-    const std::string key = tune_key((int)b->reps.size(), b->ntasks, b->nmerge, b->measure);
+    const std::string key = tune_key((int)b->reps.size(), b->ntasks, b->nmerge, b->measure, b->any_clock);
     LaunchShape best;
     bool cached = false;
     {
@@ -1461,7 +1462,7 @@ int sw_batch_autotune(sw_batch *b, int n, int *shape_out)
         }
     }
     if (!cached) {
-        int rc = autotune_shape(&best, n, [&](const LaunchShape &trial, int nn, double *ms) {
+        int rc = autotune_shape(&best, n, b->any_clock, [&](const LaunchShape &trial, int nn, double *ms) {
             return batch_timed_sweeps(b, trial, nn, ms);
         });
         if (rc != SW_OK) return rc;

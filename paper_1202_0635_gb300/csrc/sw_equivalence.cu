@@ -152,7 +152,7 @@ cudaError_t equivalence_sweep(const Batch &b, const Lattice &lat, int method, in
     const long long N = (long long)lat.L * lat.L;
     const int blocks = (int)std::max<long long>(1, std::min<long long>((N + kEqThreads - 1) / kEqThreads,
                                                                        (long long)sm_count * 8));
-    cudaError_t e = launch_bonds(b, false, sm_count, s);
+    cudaError_t e = launch_bonds(b, sm_count, s);
     if (e != cudaSuccess) return e;
     k_eq_init<<<blocks, kEqThreads, 0, s>>>(lat, hawick ? R : nullptr);
     int n = 0;

@@ -65,8 +65,8 @@ struct LaunchShape {
 constexpr int kMaxStages = 4;
 cudaError_t launch_sweep(const Batch &b, bool measure, bool labels, int sm_count, const LaunchShape &shape,
                          cudaStream_t s, cudaEvent_t *ev = nullptr);
-// The bond kernel alone (the first stage of a sweep).
-cudaError_t launch_bonds(const Batch &b, bool measure, int sm_count, cudaStream_t s);
+// The bond kernel alone, update only (the bonds of the comparator labelings).
+cudaError_t launch_bonds(const Batch &b, int sm_count, cudaStream_t s);
 
 // Comparator labelings of the paper's GPU design (Sec. 3), whole-lattice
 // iterations until no label changes.

@@ -1616,15 +1616,11 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
     return cudaGetLastError();
 }
 
-cudaError_t launch_bonds(const Batch &b, bool measure, int sm_count, cudaStream_t s)
+cudaError_t launch_bonds(const Batch &b, int sm_count, cudaStream_t s)
 {
     const int blocks = std::max(1, std::min(b.ntasks, sm_count * kBondBlocksPerSM));
-    if (measure)
-        b.any_clock ? k_bonds<true, true><<<blocks, kBlockThreads, 0, s>>>(b)
-                    : k_bonds<true, false><<<blocks, kBlockThreads, 0, s>>>(b);
-    else
-        b.any_clock ? k_bonds<false, true><<<blocks, kBlockThreads, 0, s>>>(b)
-                    : k_bonds<false, false><<<blocks, kBlockThreads, 0, s>>>(b);
+    b.any_clock ? k_bonds<false, true><<<blocks, kBlockThreads, 0, s>>>(b)
+                : k_bonds<false, false><<<blocks, kBlockThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -149,7 +149,9 @@ def test_autotune_picks_a_cached_shape_and_keeps_the_chain():
     shape = sw.sw_autotune(lat.h, 2)
     assert all(1 <= v <= 64 for v in shape)
     t = lat.sweep_index
-    assert t == 2 * (3 + 4 + 4 + 4)          # every candidate ran real sweeps
+    # Every candidate ran real sweeps: labeling 3, merge 4, flip 4 (a Potts
+    # sweep launches no bond kernel, so its figure is not tuned).
+    assert t == 2 * (3 + 4 + 4)
     o = Oracle(256, 3, POTTS, Tc, 4, init="random")
     o.sweep(t)
     assert np.array_equal(lat.spins, o.spins)
@@ -158,6 +160,10 @@ def test_autotune_picks_a_cached_shape_and_keeps_the_chain():
     assert again.sweep_index == 0
     lat.close()
     again.close()
+    clk = sw.Lattice(128, 6, sw.SW_CLOCK, 0.9, 6, init=sw.SW_INIT_RANDOM)
+    sw.sw_autotune(clk.h, 1)
+    assert clk.sweep_index == 3 + 4 + 4 + 4   # a clock sweep's bond kernel is tuned as well
+    clk.close()
     b = sw.Batch()
     for L in (32, 96, 160):
         b.add(L, 2, sw.SW_POTTS, 1.0 / math.log(1.0 + math.sqrt(2.0)), L, init=sw.SW_INIT_RANDOM)
