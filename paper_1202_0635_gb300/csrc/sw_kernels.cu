@@ -657,10 +657,11 @@ struct RowMasks {
 //   open     a component reaching the tile border (left and top edges
 //            always, right and bottom edges through an active crossing
 //            bond) continues in the neighbouring tile.
-//   settle   every provisional label points at its root; a closed root
-//            draws its cluster's new state (Sec. 2 steps (v)-(vii); clock:
-//            the reflection flag, Sec. 4); an open root takes a slot and
-//            becomes a node of the global union-find.
+//   settle   a closed root draws its cluster's new state (Sec. 2 steps
+//            (v)-(vii); clock: the reflection flag, Sec. 4); an open root
+//            takes a slot and becomes a node of the global union-find; then
+//            every other provisional label takes its root's resolved word
+//            (with debug labels: points at its root).
 //   codes    every site gets its cluster's 2-byte code, 0x100 | new state
 //            (closed Potts), 0x100 | reflection flag (closed clock) or the
 //            open slot; the open slots of the right and left edge sites go
@@ -917,9 +918,10 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
         }
         __syncthreads();
 
-        // ===== settle: every provisional label points at its root; a closed
-        // root draws, an open root takes a slot.  A settled root's word is
-        // resolved; walks stop there.
+        // ===== settle: a closed root draws, an open root takes a slot; its
+        // word becomes resolved.  Then every other provisional label takes
+        // the resolved word of its root (debug labels: its root's index, in
+        // one pass whose walks stop at a root, settled or not).
         // One-bit cluster draws (bit_draw): the STATE_BIT bits of the tile's
         // sites, eight words per tile row from the two draws that cover the
         // row, in the room of the scan masks (free after the open phase).
@@ -940,18 +942,22 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
             for (int i = threadIdx.x; i < nlab; i += blockDim.x) {
                 const int v = rlist[i];
                 int x = v;
-                bool found = false;
-                for (int it = 0; it < cap; ++it) {   // read-only: stops at a root, settled or not
-                    const int p = X[x];
-                    if (p == x || p >= kTileResolved) {
-                        found = true;
-                        break;
+                if (LABELS) {
+                    bool found = false;
+                    for (int it = 0; it < cap; ++it) {   // read-only: stops at a root, settled or not
+                        const int p = X[x];
+                        if (p == x || p >= kTileResolved) {
+                            found = true;
+                            break;
+                        }
+                        x = p;
                     }
-                    x = p;
-                }
-                if (!found) record_error(lat.st, kErrFindCap, Y0 * L + X0);
-                if (x != v) {
-                    X[v] = (uint16_t)x;
+                    if (!found) record_error(lat.st, kErrFindCap, Y0 * L + X0);
+                    if (x != v) {
+                        X[v] = (uint16_t)x;
+                        continue;
+                    }
+                } else if (X[v] != v) {   // not a root: takes its root's word below
                     continue;
                 }
                 const int g = tile_site(L, bx, by, v);
@@ -981,12 +987,38 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
                 }
                 X[v] = (uint16_t)w;
             }
+            if (!LABELS) {
+                // Every other label takes its cluster's resolved word, so a
+                // node's word leads to it in one step.
+                __syncthreads();
+                for (int i = threadIdx.x; i < nlab; i += blockDim.x) {
+                    const int v = rlist[i];
+                    int x = X[v];
+                    if (x >= kTileResolved) continue;   // a root
+                    bool found = false;
+                    for (int it = 0; it < cap; ++it) {   // resolved words: roots, or labels already done
+                        const int p = X[x];
+                        if (p >= kTileResolved) {
+                            x = p;
+                            found = true;
+                            break;
+                        }
+                        x = p;
+                    }
+                    if (!found) {
+                        record_error(lat.st, kErrFindCap, Y0 * L + X0);
+                        x = kTileResolved | kCodeClosed;
+                    }
+                    X[v] = (uint16_t)x;
+                }
+            }
         }
         __syncthreads();
 
         // ===== codes: warp = quadrant, four rows of 32 columns a step, lane =
         // four columns; a node's word leads to its cluster's resolved word in
-        // at most two more steps (label -> root).  Edge slots.
+        // at most one more step (its label), two with debug labels (label ->
+        // root).  Edge slots.
         if (qa) {
             const int c4 = 4 * (lane & 7);
             const bool cv = c4 < ncols;   // ncols % 4 == 0
@@ -997,9 +1029,10 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
                 const uint2 w2 = *reinterpret_cast<const uint2 *>(X + v0);
                 int wv[4] = {(int)(w2.x & 0xFFFFu), (int)(w2.x >> 16), (int)(w2.y & 0xFFFFu), (int)(w2.y >> 16)};
                 int rt[4] = {v0, v0 + 1, v0 + 2, v0 + 3};
-                // label -> root -> resolved word: two rounds of independent loads
+                // label -> root -> resolved word: two rounds of independent
+                // loads (one where every label holds its resolved word)
 #pragma unroll
-                for (int it = 0; it < 2; ++it) {
+                for (int it = 0; it < (LABELS ? 2 : 1); ++it) {
 #pragma unroll
                     for (int h = 0; h < 4; ++h)
                         if (wv[h] < kTileResolved) {
