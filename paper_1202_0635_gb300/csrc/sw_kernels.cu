@@ -32,6 +32,8 @@
 //                  spins, counts states and the clusters rooted in the tile;
 //                  its last block advances the sweep index of every lattice
 //                  of the batch.
+#include <type_traits>
+
 #include "sw_internal.h"
 
 namespace swgb {
@@ -1227,7 +1229,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
 {
     // New state (Potts) or reflection flag (clock) of each open slot; then
     // entry kCodeClosed + s = s, so that a Potts code indexes its new state.
-    __shared__ __align__(16) unsigned char tab[kOpenSlots + SW_MAX_Q];
+    __shared__ __align__(16) unsigned char tab[2 * kOpenSlots];
     __shared__ int rootg[LABELS ? kOpenSlots : 1];
     __shared__ unsigned int hist_state[SW_MAX_Q + 1];
     __shared__ unsigned int red[32];
@@ -1242,8 +1244,9 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
     unsigned int open_roots = 0;   // clusters reaching a tile border, counted at their root
     OpenTally tl;                  // labeling statistics of the root walks
     int cur = -1;
-    static_assert(kCodeClosed == kOpenSlots && SW_MAX_Q <= 128, "codes index the table");
-    for (int k = threadIdx.x; k < SW_MAX_Q; k += blockDim.x) tab[kOpenSlots + k] = (unsigned char)k;
+    // Codes are below 2 * kOpenSlots (kCodeMask): entries past the states are never used.
+    static_assert(kCodeClosed == kOpenSlots && SW_MAX_Q <= 128 && kCodeMask < 2 * kOpenSlots, "codes index the table");
+    for (int k = threadIdx.x; k < kOpenSlots; k += blockDim.x) tab[kOpenSlots + k] = (unsigned char)(k < SW_MAX_Q ? k : 0);
     auto flush = [&]() {
         if (STATS && cur >= 0) flush_open_tally<kBlockThreads>(lat.stats, tl, 0u, red);
         tl = OpenTally();
@@ -1347,51 +1350,59 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
         }
         __syncthreads();
 
+        // The spin writes, with the state counts the lattice needs compiled
+        // into each form (CM 1: q = 2, CM 2: q <= 8, CM 0: none here).
+        auto write_chunks = [&](auto cm) {
+            constexpr int CM = decltype(cm)::value;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int rr = crow + 32 * j;
-            if (!(rr < th && cn > 0)) continue;
-            const size_t site0 = (size_t)(Y0 + rr) * L + X0 + ccol;
-            const uint32_t cws[8] = {cwa[j].x, cwa[j].y, cwa[j].z, cwa[j].w, cwb[j].x, cwb[j].y, cwb[j].z, cwb[j].w};
-            const uint32_t sws[4] = {swv[j].x, swv[j].y, swv[j].z, swv[j].w};
-            uint32_t out[4];
+            for (int j = 0; j < 2; ++j) {
+                const int rr = crow + 32 * j;
+                if (!(rr < th && cn > 0)) continue;
+                const size_t site0 = (size_t)(Y0 + rr) * L + X0 + ccol;
+                const uint32_t cws[8] = {cwa[j].x, cwa[j].y, cwa[j].z, cwa[j].w, cwb[j].x, cwb[j].y, cwb[j].z, cwb[j].w};
+                const uint32_t sws[4] = {swv[j].x, swv[j].y, swv[j].z, swv[j].w};
+                uint32_t out[4];
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                uint32_t word = 0;
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t word = 0;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const uint32_t code = (cws[2 * g + (h >> 1)] >> (16 * (h & 1))) & 0xFFFFu;
-                    int ns;
-                    if (clock) {   // closed: the cluster's flag in the code; open: its root's, in the table
-                        const int k0 = valid_state((int)((sws[g] >> (8 * h)) & 0xFFu), q);
-                        ns = ((code & kCodeClosed) ? (code & 1u) : tab[code & 0xFFu]) ? reflect(k0, m, q) : k0;
-                    } else {
-                        ns = tab[min(code, (uint32_t)(kOpenSlots + SW_MAX_Q - 1))];   // open slot or kCodeClosed | state
+                    for (int h = 0; h < 4; ++h) {
+                        const uint32_t code = (cws[2 * g + (h >> 1)] >> (16 * (h & 1))) & (uint32_t)kCodeMask;
+                        int ns;
+                        if (clock) {   // closed: the cluster's flag in the code; open: its root's, in the table
+                            const int k0 = valid_state((int)((sws[g] >> (8 * h)) & 0xFFu), q);
+                            ns = ((code & kCodeClosed) ? (code & 1u) : tab[code & 0xFFu]) ? reflect(k0, m, q) : k0;
+                        } else {
+                            ns = tab[code];   // open slot or kCodeClosed | state
+                        }
+                        if (CM == 2 && 4 * g < cn) {
+                            const unsigned long long one = 1ull << (16 * (ns & 3));
+                            if (ns < 4) cnt_lo += one;
+                            else cnt_hi += one;
+                        }
+                        if (LABELS && 4 * g < cn && !(code & kCodeClosed))
+                            lat.label[site0 + 4 * g + h] = rootg[LABELS ? (code & 0xFF) : 0];
+                        word |= (uint32_t)(ns & 0xFF) << (8 * h);
                     }
-                    if (MEASURE && q > 2 && q <= 8 && 4 * g < cn) {
-                        const unsigned long long one = 1ull << (16 * (ns & 3));
-                        if (ns < 4) cnt_lo += one;
-                        else cnt_hi += one;
+                    out[g] = word;
+                    if (CM == 1 && 4 * g < cn) {   // states are 0 or 1
+                        cnt_lo += (unsigned)__popc(word);
+                        cnt_hi += 4u;
                     }
-                    if (LABELS && 4 * g < cn && !(code & kCodeClosed))
-                        lat.label[site0 + 4 * g + h] = rootg[LABELS ? (code & 0xFF) : 0];
-                    word |= (uint32_t)(ns & 0xFF) << (8 * h);
                 }
-                out[g] = word;
-                if (MEASURE && q == 2 && 4 * g < cn) {   // states are 0 or 1
-                    cnt_lo += (unsigned)__popc(word);
-                    cnt_hi += 4u;
+                if (vec) {
+                    *reinterpret_cast<uint4 *>(lat.spin + site0) = make_uint4(out[0], out[1], out[2], out[3]);
+                } else {
+                    uint32_t *sp = reinterpret_cast<uint32_t *>(lat.spin + site0);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+                        if (4 * g < cn) sp[g] = out[g];
                 }
             }
-            if (vec) {
-                *reinterpret_cast<uint4 *>(lat.spin + site0) = make_uint4(out[0], out[1], out[2], out[3]);
-            } else {
-                uint32_t *sp = reinterpret_cast<uint32_t *>(lat.spin + site0);
-#pragma unroll
-                for (int g = 0; g < 4; ++g)
-                    if (4 * g < cn) sp[g] = out[g];
-            }
-        }
+        };
+        if (MEASURE && q == 2) write_chunks(std::integral_constant<int, 1>());
+        else if (MEASURE && q <= 8) write_chunks(std::integral_constant<int, 2>());
+        else write_chunks(std::integral_constant<int, 0>());
         if (MEASURE && q > 8) {
             // Many states: warp-aggregated shared histogram, site by site.
 #pragma unroll 1
