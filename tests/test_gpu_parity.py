@@ -137,8 +137,11 @@ def test_graph_mode_matches_direct_launches():
     run_lockstep(120, 6, CLOCK, 0.9, 3, "random", 40, graph=True, every=5)
 
 
-def test_update_only_mode_keeps_the_chain():
-    g, o = make_pair(96, 2, ISING, TC_ISING, 11, "random")
+@pytest.mark.parametrize("model,q,T", [(ISING, 2, TC_ISING), (POTTS, 4, tc_potts(4)), (POTTS, 12, tc_potts(12)),
+                                       (CLOCK, 6, 0.9), (CLOCK, 16, 0.5)])
+def test_update_only_mode_keeps_the_chain(model, q, T):
+    """Measurement off: the spin writes compiled without state counts."""
+    g, o = make_pair(96, q, model, T, 11, "random")
     sw.sw_set_measure(g.h, 0)
     g.sweep(30)
     o.sweep(30)
