@@ -803,17 +803,26 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
             const int c = lane;
             int lab = 0;
             uint16_t *pl = X + QW * qy * TW + QW * qx + c;
-            for (int r0 = 0; r0 < nrows; r0 += 4) {
+            const RowMasks *ms = &sm[QW * qy][qx];
+            const int nb0 = QW * qy * TW + QW * qx;
+            auto scan_row = [&](int r) {
+                const RowMasks m = ms[2 * r];
+                const int s0 = run_start(m.S, c);
+                const bool hooked = (m.HS >> s0) & 1u;
+                const int fc = s0 + __ffs(m.H >> s0) - 1;
+                const int up = __shfl_sync(FULL, lab, fc & 31);
+                lab = hooked ? up : nb0 + r * TW + s0;
+                pl[r * TW] = (uint16_t)lab;
+            };
+            // A whole quadrant unrolled: every row offset is a constant (the
+            // kernel that draws the bonds has no registers to spare for it).
+            if (!FUSED && nrows == QW) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int r = r0 + j;
-                    const RowMasks m = sm[QW * qy + r][qx];
-                    const int s0 = run_start(m.S, c);
-                    const bool hooked = (m.HS >> s0) & 1u;
-                    const int fc = s0 + __ffs(m.H >> s0) - 1;
-                    const int up = __shfl_sync(FULL, lab, fc & 31);
-                    lab = hooked ? up : (QW * qy + r) * TW + QW * qx + s0;
-                    pl[r * TW] = (uint16_t)lab;
+                for (int r = 0; r < QW; ++r) scan_row(r);
+            } else {
+                for (int r0 = 0; r0 < nrows; r0 += 4) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) scan_row(r0 + j);
                 }
             }
         }
@@ -1024,6 +1033,8 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
         if (qa) {
             const int c4 = 4 * (lane & 7);
             const bool cv = c4 < ncols;   // ncols % 4 == 0
+            // Unrolled (loads of several steps in flight) where registers allow.
+#pragma unroll(FUSED ? 1 : 4)
             for (int r = lane >> 3; r < nrows; r += 4) {
                 const int row2 = QW * qy + r;
                 const int v0 = row2 * TW + QW * qx + c4;
