@@ -139,16 +139,21 @@ __device__ __forceinline__ void add_hist_any(unsigned int *hist, int v, bool val
 }
 
 // The kernels of a sweep are launched with programmatic stream
-// serialization: each waits here until the previous kernel has completed and
-// its writes are visible (nothing before this point touches memory), then
-// lets the next kernel of the stream launch, so that its blocks take the
-// SMs this kernel's last blocks leave and wait there instead of being
-// launched after the grid drains.  (Launched without the attribute, both
-// do nothing.)
+// serialization.  pdl_wait: until the previous kernel has completed and its
+// writes are visible.  pdl_release: the next kernel of the stream may
+// launch, so that its blocks take the SMs this kernel's last blocks leave
+// and wait there instead of being launched after the grid drains; a block
+// of the next kernel runs only once every block of this one has released
+// or exited, i.e. has passed its own wait, so whatever the kernel before
+// this one wrote is visible to it before it waits.  (Launched without the
+// attribute, both do nothing.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Nothing before this point touches memory.
 __device__ __forceinline__ void pdl_begin()
 {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait();
+    pdl_release();
 }
 
 // Per-lattice values every block needs once per task.
@@ -1205,6 +1210,7 @@ template <bool MEASURE>
 __device__ void finish_sweep(const Batch &b)
 {
     __shared__ int s_last;
+    pdl_wait();   // (the flip kernel waits late; also where a block had no tile to flip)
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -1247,7 +1253,7 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
 
-    pdl_begin();
+    pdl_release();   // the wait comes after the first codes are loaded
     const int r = threadIdx.x & 31;
     // q <= 8: state counts of this thread, 16 bits per state (states 0-3, 4-7);
     // q == 2: sites in cnt_hi, sites in state 1 in cnt_lo.
@@ -1342,6 +1348,9 @@ __global__ void __launch_bounds__(kBlockThreads, ANY_CLOCK ? kFlipResidentClock 
                 }
             }
         }
+        // The codes above are the labeling kernel's, two launches back; the
+        // union-find entries below are the merge's: wait for it here.
+        pdl_wait();
         // Every open component of the tile belongs to a cluster whose root
         // (the component with the cluster's smallest site, after the merge)
         // draws the new state (Potts) or the reflection flag (clock), Sec. 2
