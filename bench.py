@@ -540,7 +540,7 @@ def run_ours(args, world, rank, local):
             raise RuntimeError(sw.sw_last_error())
     e2e_s = time.perf_counter() - t0
     e2e_value = e2e_s * 1e9 / (ne2e * N)
-    d2h = 8 * sw.sw_ncounters(Q_BENCH, sw.SW_POTTS) + 40   # counter row + device state word block
+    d2h = 8 * sw.sw_ncounters(Q_BENCH, sw.SW_POTTS) + 48   # counter row + device state word block
 
     batched = None
     if not args.no_batched:

@@ -397,6 +397,7 @@ int reset_device_index(sw_handle *h, uint64_t t)
     st.sweep = t;
     st.stop = h->stop;
     st.classes_upto = t;   // the current configuration is not a sweep result of this run
+    st.next_t = t;
     SW_CUDA(cudaMemcpyAsync(h->d_st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
     SW_CUDA(cudaMemsetAsync(h->d_ring, 0, sizeof(unsigned long long) * swgb::kRingSlots * h->ncounters, h->stream));
     SW_CUDA(cudaStreamSynchronize(h->stream));
@@ -1652,6 +1653,7 @@ extern "C" int sw_sweep_noalloc(int L, int q, int model, double T, uint64_t seed
     st.sweep = sweep0;
     st.stop = swgb::kNoStop;
     st.classes_upto = sweep0;
+    st.next_t = sweep0;
     SW_CUDA(cudaMemcpyAsync(lat.st, &st, sizeof st, cudaMemcpyHostToDevice, s));
     SW_CUDA(cudaMemsetAsync(b.ticket, 0, sizeof(unsigned int), s));
     SW_CUDA(cudaMemsetAsync(lat.ring, 0, sizeof(unsigned long long) * kNoallocRingSlots * nc, s));

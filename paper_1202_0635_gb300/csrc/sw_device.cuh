@@ -30,6 +30,9 @@ struct DevState {
     int err;                           // first device error (kErr*)
     int err_where;                     // site or index that hit it
     unsigned int scratch;              // host-side checks (count of invalid spins)
+    unsigned int pad;
+    unsigned long long next_t;         // sweep index the next labeling kernel will run at (the merge
+                                       // kernel writes it; a hint for early bond draws, checked)
 };
 
 // Everything a kernel needs about one lattice.  Passed by value.

@@ -403,20 +403,13 @@ __device__ __forceinline__ void load_half_rows(const int8_t *spin, int L, int y,
 // bond's lane of the site pair's BOND draw lies below the threshold.  eqR /
 // eqD: the equal-neighbour masks.  rowbase: index of the half row's first
 // site (even).  UNROLL: draws in flight per thread (registers vs overlap).
+// The draws alone (they need no states): bit c of rR / rD is set iff the
+// right / lower bond of site c would be active between equal states.
 template <int UNROLL>
-__device__ __forceinline__ void potts_bonds(const Lattice &lat, unsigned long long t, size_t rowbase, int ncols,
-                                            bool rv, const uint32_t (&wd)[8], const uint32_t (&dn)[8], uint32_t sr,
-                                            unsigned &R, unsigned &D, unsigned &eqR, unsigned &eqD)
+__device__ __forceinline__ void potts_draws(const Lattice &lat, unsigned long long t, size_t rowbase, int ncols,
+                                            bool rv, unsigned &rR, unsigned &rD)
 {
-    const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
-    eqR = eqD = 0u;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
-        eqR |= zero_bytes4(wd[k] ^ __funnelshift_r(wd[k], nxt, 8)) << (4 * k);
-        eqD |= zero_bytes4(wd[k] ^ dn[k]) << (4 * k);
-    }
-    unsigned rR = 0u, rD = 0u;
+    rR = rD = 0u;
     if (rv) {
         const uint32_t pbase = (uint32_t)(rowbase >> 1);
         const uint32_t thr = lat.thr;
@@ -429,6 +422,31 @@ __device__ __forceinline__ void potts_bonds(const Lattice &lat, unsigned long lo
             }
         }
     }
+}
+
+// The equal-neighbour masks of the half row (the states are dead after it,
+// before the draws).
+__device__ __forceinline__ void potts_equal(int ncols, const uint32_t (&wd)[8], const uint32_t (&dn)[8], uint32_t sr,
+                                            unsigned &eqR, unsigned &eqD)
+{
+    eqR = eqD = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t nxt = (k < 7 && 4 * k + 4 < ncols) ? wd[(k + 1) & 7] : sr;
+        eqR |= zero_bytes4(wd[k] ^ __funnelshift_r(wd[k], nxt, 8)) << (4 * k);
+        eqD |= zero_bytes4(wd[k] ^ dn[k]) << (4 * k);
+    }
+}
+
+template <int UNROLL>
+__device__ __forceinline__ void potts_bonds(const Lattice &lat, unsigned long long t, size_t rowbase, int ncols,
+                                            bool rv, const uint32_t (&wd)[8], const uint32_t (&dn)[8], uint32_t sr,
+                                            unsigned &R, unsigned &D, unsigned &eqR, unsigned &eqD)
+{
+    const unsigned V = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
+    potts_equal(ncols, wd, dn, sr, eqR, eqD);
+    unsigned rR, rD;
+    potts_draws<UNROLL>(lat, t, rowbase, ncols, rv, rR, rD);
     R = rv ? (rR & eqR & V) : 0u;
     D = rv ? (rD & eqD & V) : 0u;
 }
@@ -695,11 +713,38 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
     __shared__ unsigned int red[32];
     __shared__ __align__(16) Lattice lat;
     __shared__ TaskCtx ctx;
+    __shared__ unsigned long long s_pre_t;   // FUSED: sweep index of the first tile's early draws
 
-    pdl_begin();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qx = warp & 1, qy = warp >> 1;
     const int row = QW * qy + lane;   // my tile row (lane = row phases)
+    const int nrep = __ldg(&b.dev->nrep), ntasks = __ldg(&b.dev->ntasks);
+    if (FUSED) {
+        // Before the wait for the previous kernel: the bond draws of the
+        // block's first tile need only the sweep index, which the merge
+        // kernel of the previous sweep announced (next_t; that kernel has
+        // completed once this block runs).  Kept in the room of the union
+        // list until the first masks phase, used there if the index holds.
+        if (threadIdx.x == 0) s_pre_t = ~0ull;
+        if ((int)blockIdx.x < ntasks) {
+            const int rep0 = find_rep(b.task_off, nrep, (int)blockIdx.x);
+            load_lattice(&lat, b.lat + rep0);
+            __syncthreads();
+            const unsigned long long t0 = read_u64(&lat.st->next_t);
+            const int tile = (int)blockIdx.x - __ldg(b.task_off + rep0);
+            const int by = tile / lat.tiles_x, bx = tile - by * lat.tiles_x;
+            const int X0 = bx * TW, Y0 = by * TH;
+            const int ncols = max(0, min(QW, min(TW, lat.L - X0) - QW * qx));
+            const int nrows = max(0, min(QW, min(TH, lat.L - Y0) - QW * qy));
+            const bool rv = ncols > 0 && lane < nrows;
+            unsigned rR, rD;
+            potts_draws<kFusedDrawUnroll>(lat, t0, (size_t)(Y0 + row) * lat.L + X0 + QW * qx, ncols, rv, rR, rD);
+            upairs[threadIdx.x] = rR;
+            upairs[kBlockThreads + threadIdx.x] = rD;
+            if (threadIdx.x == 0) s_pre_t = t0;
+        }
+    }
+    pdl_begin();
 
     unsigned int closed_roots = 0;
     unsigned int active = 0, unequal = 0, pairs = 0;   // FUSED: k_bonds' counters
@@ -722,7 +767,6 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
         __syncthreads();
     };
 
-    const int nrep = __ldg(&b.dev->nrep), ntasks = __ldg(&b.dev->ntasks);
     for (int task = blockIdx.x; task < ntasks; task += gridDim.x) {
         const int rep = find_rep(b.task_off, nrep, task);
         if (rep != cur) {
@@ -760,8 +804,16 @@ __global__ void __launch_bounds__(kBlockThreads, FUSED ? kLabelResidentFused : 1
                 const int y = Y0 + row, x0 = X0 + QW * qx;
                 uint32_t wd[8], dn[8], sr;
                 load_half_rows(lat.spin, L, y, x0, ncols, rv, wd, dn, sr);
-                unsigned eqR, eqD;
-                potts_bonds<kFusedDrawUnroll>(lat, t, (size_t)y * L + x0, ncols, rv, wd, dn, sr, R, D, eqR, eqD);
+                unsigned eqR, eqD, rR, rD;
+                potts_equal(ncols, wd, dn, sr, eqR, eqD);
+                if (task == (int)blockIdx.x && t == s_pre_t) {   // the early draws hold (uniform in the block)
+                    rR = upairs[threadIdx.x];
+                    rD = upairs[kBlockThreads + threadIdx.x];
+                } else {
+                    potts_draws<kFusedDrawUnroll>(lat, t, (size_t)y * L + x0, ncols, rv, rR, rD);
+                }
+                R = rv ? (rR & eqR & V) : 0u;
+                D = rv ? (rD & eqD & V) : 0u;
                 if (MEASURE) {
                     active += __popc(R) + __popc(D);
                     if (ctx.count_classes && rv) {
@@ -1109,7 +1161,22 @@ template <bool STATS>
 __global__ void __launch_bounds__(256, 8) k_merge(Batch b)
 {
     static_assert(kMergeItems == TH + TW, "merge items: right edge rows, then bottom edge columns");
-    pdl_begin();
+    pdl_wait();
+    {   // The sweep index the next labeling kernel runs at, announced before
+        // this kernel lets the flip launch (the labeling kernel of this sweep
+        // has completed: all its blocks have read the previous value).
+        bool wrote = false;
+        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < __ldg(&b.dev->nrep); r += gridDim.x * blockDim.x) {
+            DevState *st = b.lat[r].st;
+            const unsigned long long t = read_u64(&st->sweep);
+            if (t < read_u64(&st->stop)) {
+                *reinterpret_cast<volatile unsigned long long *>(&st->next_t) = t + 1;
+                wrote = true;
+            }
+        }
+        if (wrote) __threadfence();
+    }
+    pdl_release();
     long long lo = 0, hi = 0;
     int rep = -1;
     const Lattice *lp = b.lat;   // read through the L1, not copied into registers
