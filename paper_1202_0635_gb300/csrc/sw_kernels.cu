@@ -25,7 +25,9 @@
 //                  root's site index.
 //   k_merge        joins the open roots across every active bond that
 //                  crosses a tile edge or the periodic wrap (atomicMin,
-//                  larger root under smaller).
+//                  larger root under smaller); first it announces the sweep
+//                  index of the next labeling launch, which draws its first
+//                  bonds before it waits for the flip.
 //   k_flip_tiles   finds the cluster root of every open component (the
 //                  smallest site index of the cluster, Sec. 2 "proper
 //                  label"), which draws the cluster's new state; writes all
