@@ -193,7 +193,7 @@ int sw_get_sweep_limit(sw_handle *h, uint64_t *out);
 
 /* Launch shape: resident blocks per SM requested for the kernels of a
  * sweep, shape[4] = {labeling, merge, flip, bonds}, each in [1, 64]
- * (default {11, 16, 10, 16}).  The labeling kernel that draws the bonds
+ * (default {11, 12, 10, 16}).  The labeling kernel that draws the bonds
  * itself (batches without a clock lattice) keeps at most 11 blocks per SM,
  * the flip kernel 10 (8 with a clock lattice); the bond figure applies only
  * where the bond kernel runs (a clock lattice in the batch).

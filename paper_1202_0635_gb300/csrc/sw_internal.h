@@ -58,7 +58,7 @@ cudaError_t launch_count_invalid(const Lattice &lat, unsigned int *bad, int sm_c
 // labeling, merge, flip and bond kernels (the grids never exceed the work).
 // Any shape gives the same results; only the speed differs.
 struct LaunchShape {
-    int label = 11, merge = 16, flip = 10, bonds = kBondBlocksPerSM;
+    int label = 11, merge = 12, flip = 10, bonds = kBondBlocksPerSM;
 };
 // ev (optional): events recorded before the first and after every kernel of
 // the sweep (kMaxStages + 1 entries): bonds, labeling, merge, flip.
